@@ -1,0 +1,347 @@
+"""Throughput benchmark: single-step ESSFM DBP over a 3200 km link vs 20-step SSFM.
+
+Workload (one "step" = one pass of the whole DBP hot path over one batch):
+  B waveforms of 28 GBaud PM-QPSK, 2^18 symbols at 2 samples/symbol (2 x 524288
+  complex64 samples each), 40 x 80 km of SMF (3200 km), single-step ESSFM with N_c = 32
+  (the headline) and 20-step SSFM (reported beside it).  Inputs are resident in HBM
+  and the working set (B = 128: 1 GiB in + 1 GiB out) is far larger than the 129 MB L2.
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Msamples/s DBP @3200km ESSFM-1step vs SSFM-20step; %HBM roofline; Q match"
+UNIT = "Msamples/s"
+N_SYMBOLS = 2 ** 18
+N_SAMPLES = N_SYMBOLS * synth.SPS
+N_SPANS = 40
+LAUNCH_DBM = 2.0
+ESSFM_TAPS = 32
+BYTES_PER_VSAMPLE = 32          # 2 pols x complex64 read + 2 pols x complex64 written
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+NCU_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def essfm_coeffs(nc: int) -> np.ndarray:
+    """Fixed decaying ESSFM filter (values do not change the work done)."""
+    c = 0.6 * np.exp(-np.arange(nc + 1) / 10.0)
+    return (c / (c[0] + 2 * c[1:].sum())).astype(np.float32)
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def load_traffic(key):
+    try:
+        with open(NCU_TRAFFIC) as f:
+            return json.load(f).get(key)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, f[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def smi_index(local: int) -> int:
+    """nvidia-smi index of this process's GPU."""
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        parts = [p.strip() for p in cvd.split(",")]
+        if local < len(parts) and parts[local].isdigit():
+            return int(parts[local])
+    return local
+
+
+# ---------------------------------------------------------------------- GPU arm
+def make_plan(method, n_wave, fft_size):
+    from paper_1507_00921_gb300 import Plan
+    link = synth.link(N_SPANS)
+    if method == "essfm":
+        return Plan(link, synth.SAMPLE_RATE, N_SAMPLES, n_waveforms=n_wave, method="essfm", n_steps=1,
+                    n_taps=ESSFM_TAPS, coeffs=essfm_coeffs(ESSFM_TAPS), fft_size=fft_size)
+    return Plan(link, synth.SAMPLE_RATE, N_SAMPLES, n_waveforms=n_wave, method="ssfm", n_steps=20,
+                fft_size=fft_size)
+
+
+def time_device(torch, plan, x, y, steps, warmup, stream):
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            plan.run(x, y, stream=stream)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.run(x, y, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def autotune(torch, method, n_wave, x, y, stream, candidates=(2048, 4096, 8192)):
+    best = None
+    for n in candidates:
+        try:
+            plan = make_plan(method, n_wave, n)
+        except Exception:
+            continue
+        t = time_device(torch, plan, x, y, 5, 2, stream)
+        plan.close()
+        if best is None or t < best[1]:
+            best = (n, t)
+    return best[0]
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B = args.batch
+    x_host = synth.received_like(B, N_SYMBOLS, LAUNCH_DBM, seed=synth.BASE_SEED + 2 + 97 * rank, distinct=8)
+    x = torch.from_numpy(x_host).cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.Stream()
+    fft_e = args.fft_size or autotune(torch, "essfm", B, x, y, stream)
+    fft_s = args.fft_size or autotune(torch, "ssfm", B, x, y, stream, candidates=(2048, 4096, 8192))
+    pe = make_plan("essfm", B, fft_e)
+    ps = make_plan("ssfm", B, fft_s)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    # ---- headline: ESSFM N_s = 1
+    for _ in range(args.warmup):
+        pe.run(x, y, stream=stream)
+    barrier()
+    with ClockSampler(smi_index(local)) as clk:
+        t_e = time_device(torch, pe, x, y, args.steps, 0, stream)
+    barrier()
+    clocks = clk.summary()
+    # ---- 20-step SSFM, same workload
+    k_s = max(3, args.steps // 20)
+    t_s = time_device(torch, ps, x, y, k_s, max(3, args.warmup // 4), stream)
+    barrier()
+    times = torch.tensor([t_e, t_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    t_e, t_s = times.tolist()
+
+    vs = B * N_SAMPLES                    # vector samples per rank per step
+    value = world * vs * args.steps / t_e / 1e6
+    ssfm_value = world * vs * k_s / t_s / 1e6
+    launch_s = t_e / args.steps           # one kernel per step
+    achieved = BYTES_PER_VSAMPLE * vs / launch_s / 1e9
+    peak, peak_kind = hbm_peak()
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    k_e2e = max(3, min(20, args.steps // 50))
+    xh = torch.from_numpy(x_host).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    pe.run_host(xh, yh)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        pe.run_host(xh, yh)
+    barrier()
+    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_value = world * vs * k_e2e / t_e2e.item() / 1e6
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds, fft_e)
+    if rank == 0:
+        info = pe.info
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_e / args.steps * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"3200km (40x80 km SMF) PM-QPSK 28 GBaud, 2^18 symbols x 2 sps per waveform, "
+                                   f"ESSFM N_s=1 N_c={ESSFM_TAPS}",
+                       "n_waveforms_per_gpu": B, "samples_per_waveform": N_SAMPLES, "fft_size": fft_e,
+                       "overlap": info.overlap, "valid_per_block": info.valid,
+                       "l2": "inputs larger than L2 (working set 2 x B x 8 MiB)", "parallelism": f"dp{world}"},
+            "ssfm20": {"value": round(ssfm_value, 1), "unit": UNIT, "fft_size": fft_s,
+                       "ms_per_step": round(t_s / k_s * 1e3, 3), "steps": k_s,
+                       "essfm1_over_ssfm20": round(value / ssfm_value, 2)},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                         "traffic": load_traffic(f"essfm1_nc{ESSFM_TAPS}_N{fft_e}"),
+                         "bytes_per_vector_sample": BYTES_PER_VSAMPLE},
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(x_host.nbytes),
+                    "d2h_bytes_per_step": int(x_host.nbytes), "steps": k_e2e},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    pe.close()
+    ps.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------- CPU oracle
+def oracle_rate(seconds: float, fft_size: int, method: str = "essfm"):
+    """Time the FP64 oracle on whole overlap-save blocks of one 3200 km waveform until
+    about ``seconds`` of CPU time are spent; returns (vector samples/s, sample text)."""
+    from oracle import dbp as odbp
+    from oracle import fiber
+    link = synth.link(N_SPANS)
+    if method == "essfm":
+        cfg = fiber.make_config(link, synth.SAMPLE_RATE, 1, ESSFM_TAPS, fft_size,
+                                coeffs=essfm_coeffs(ESSFM_TAPS).astype(np.float64))
+    else:
+        cfg = fiber.make_config(link, synth.SAMPLE_RATE, 20, 0, fft_size)
+    x = synth.received_like(1, N_SYMBOLS, LAUNCH_DBM, seed=synth.BASE_SEED + 2, distinct=1)[0]
+    x = x.astype(np.complex128)
+    v, nb, _ = odbp.block_layout(N_SAMPLES, cfg.fft_size, cfg.overlap)
+    done, blocks = 0, 0
+    t0 = time.perf_counter()
+    while blocks == 0 or (time.perf_counter() - t0 < seconds and blocks < nb):
+        ids = np.arange(blocks, min(nb, blocks + 4))
+        odbp.dbp_blocks(x, cfg, ids)
+        blocks += len(ids)
+        done += len(ids) * v
+    el = time.perf_counter() - t0
+    return done / el, f"{blocks} of {nb} overlap-save blocks (N={fft_size}, {blocks * v} output vector samples) " \
+                      f"of one 2x524288-sample 3200 km waveform, {method}"
+
+
+def cpu_baseline(seconds: float, fft_size: int):
+    rate, sample = oracle_rate(seconds, fft_size)
+    return {"value": round(rate / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": sample + "; numpy float64, single thread"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    fft = args.fft_size or 4096
+    per = args.cpu_seconds / max(1, args.steps + args.warmup)
+    for _ in range(args.warmup):
+        oracle_rate(per, fft)
+    rates, samples = [], None
+    for _ in range(args.steps):
+        r, samples = oracle_rate(per, fft)
+        rates.append(r)
+    value = statistics.mean(rates) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"3200km (40x80 km SMF) PM-QPSK 28 GBaud, 2^18 symbols x 2 sps per waveform, "
+                               f"ESSFM N_s=1 N_c={ESSFM_TAPS}", "fft_size": fft},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"per step: {samples}; numpy float64, single thread"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=128, help="waveforms per GPU")
+    ap.add_argument("--fft-size", type=int, default=0, help="0 = autotune over {2048, 4096, 8192}")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

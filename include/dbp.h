@@ -1,0 +1,167 @@
+/*
+ * libdbp -- digital backpropagation (DBP) of polarization-multiplexed optical
+ * signals with the split-step Fourier method (SSFM) and the enhanced SSFM (ESSFM),
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Secondini et al., "Coherent 100G Nonlinear Compensation with Single-Step
+ * Digital Backpropagation", arXiv:1507.00921.
+ *   - Section II, Eq. 1:  linear sub-step  Y_k = X_k exp(-j 2 pi^2 beta2 f_k^2 dz)
+ *   - Section II, Eq. 2:  SSFM nonlinear sub-step  z_k = y_k exp(-j gamma dz_eff |y_k|^2)
+ *   - Section II, Eq. 3:  ESSFM nonlinear sub-step, a real symmetric filter c_0..c_Nc
+ *     over the joint intensity |y_k|^2 = |y_k,1|^2 + |y_k,2|^2 of both polarizations
+ *   - Section II, after Eq. 2:  dz_eff = (1 - exp(-alpha dz)) / alpha, steps chained
+ *   - Section III:  overlap-and-save blocks of N samples, overlap >= channel memory
+ *     M ~= 2 pi |beta2| L B^2 with B equal to the sampling rate
+ * Backpropagation applies the inverse operators (+j phases), steps running from the
+ * receiver back to the transmitter, each step linear sub-step first.
+ *
+ * Data layout: a waveform is complex64 (interleaved float re, im), polarization-major:
+ * [n_waveforms][2][n_samples].  All device buffers are owned by the caller; the plan
+ * owns its tables and scratch.  Every call returns 0 (DBP_OK) or a negative DBP_ERR_*
+ * code; nothing is printed and no call aborts the process.  Calls on one plan are not
+ * thread-safe; different plans may be used from different host threads.
+ */
+#ifndef DBP_H
+#define DBP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define DBP_OK               0
+#define DBP_ERR_ARG         -1   /* null pointer, non-positive size, bad enum value    */
+#define DBP_ERR_INFEASIBLE  -2   /* block length <= overlap, or unsupported fft_size  */
+#define DBP_ERR_ALLOC       -3   /* device or host allocation failed                  */
+#define DBP_ERR_CUDA        -4   /* a CUDA runtime call failed                        */
+#define DBP_ERR_TIMEOUT     -5   /* a bounded device wait gave up (batched launch)    */
+#define DBP_ERR_ALIAS       -6   /* output buffer overlaps the input buffer           */
+#define DBP_ERR_UNSUPPORTED -7   /* option not available in this build                */
+
+/* Enumerations. */
+#define DBP_PERIODIC   0   /* waveform is periodic outside [0, n) (circular channel)  */
+#define DBP_ZERO       1   /* waveform is zero outside [0, n)                          */
+#define DBP_SSFM       0   /* Eq. 2 nonlinear sub-step (n_taps must be 0)               */
+#define DBP_ESSFM      1   /* Eq. 3 nonlinear sub-step with n_taps = N_c coefficients   */
+#define DBP_FP32       0   /* FFT linear sub-step in FP32                               */
+
+/* Opaque stream handle: a cudaStream_t (NULL = legacy default stream). */
+typedef void *dbp_stream_t;
+
+/* The fibre link (Section II parameters; Section IV link: spans of SMF + EDFAs). */
+typedef struct {
+    int32_t n_spans;            /* number of amplified spans, >= 1                       */
+    double  span_len_m;         /* span length (m), > 0                                  */
+    double  alpha_db_per_km;    /* power attenuation (dB/km), >= 0                       */
+    double  D_ps_per_nm_km;     /* dispersion parameter D; beta2 = -D lambda^2/(2 pi c)  */
+    double  lambda_m;           /* carrier wavelength (m), > 0                           */
+    double  gamma_per_W_km;     /* Kerr coefficient gamma (1/(W km))                     */
+    double  manakov_factor;     /* multiplies gamma (8/9 for the Manakov equation)       */
+} dbp_link;
+
+/* The received signal. */
+typedef struct {
+    double  sample_rate_hz;     /* f_s; also the bandwidth B of the memory rule          */
+    int64_t n_samples;          /* samples per polarization per waveform, >= 1           */
+    int32_t n_waveforms;        /* independent waveforms in one call, >= 1               */
+    int32_t boundary;           /* DBP_PERIODIC or DBP_ZERO                              */
+} dbp_signal;
+
+/* The backpropagation steps. */
+typedef struct {
+    int32_t method;             /* DBP_SSFM or DBP_ESSFM                                 */
+    int32_t n_steps;            /* N_s >= 1; step 0 is next to the receiver              */
+    int32_t n_taps;             /* N_c, 0..DBP_MAX_TAPS (0 for DBP_SSFM)                 */
+    const float  *coeffs;       /* host; c_0..c_Nc: [n_steps][n_taps+1] if
+                                   coeffs_per_step else [n_taps+1]; NULL -> c_0 = 1, rest 0 */
+    int32_t coeffs_per_step;    /* 0 or 1                                                */
+    const double *step_len_m;   /* host [n_steps] step lengths (sum should be the link
+                                   length) or NULL for uniform L / N_s                   */
+    const double *gamma_eff;    /* host [n_steps] gamma*manakov*dz_eff overrides or NULL  */
+    int32_t fft_size;           /* N in {512,1024,2048,4096,8192}                        */
+    int32_t overlap;            /* O: 0 = rule ceil(M) + 2 N_s N_c rounded up to a
+                                   multiple of 8; else a multiple of 4 in [0, N)        */
+    int32_t precision;          /* DBP_FP32                                              */
+} dbp_steps;
+
+#define DBP_MAX_TAPS  64
+#define DBP_MAX_STEPS 1024
+
+/* Geometry and step table of a plan, computed on the host. */
+typedef struct {
+    int32_t fft_size;           /* N                                                     */
+    int32_t overlap;            /* O (even); O/2 samples discarded at each block end      */
+    int32_t valid;              /* N - O output samples per block                        */
+    int32_t n_blocks;           /* blocks per waveform = ceil(n_samples / valid)         */
+    int32_t n_steps;
+    int32_t n_taps;
+    double  beta2_s2_per_m;     /* beta2                                                 */
+    double  memory_samples;     /* M = 2 pi |beta2| L f_s^2 (Section III)                */
+    double  link_len_m;         /* L                                                     */
+} dbp_plan_info;
+
+typedef struct dbp_plan dbp_plan_t;
+
+/*
+ * Computes the plan geometry and per-step table on the host only (no CUDA call):
+ * dz_s (step lengths) and gamma_eff_s = gamma * manakov * integral over step s of the
+ * forward power profile exp(-alpha (z - z_span_start)) (equal to Section II's
+ * dz_eff = (1 - exp(-alpha dz))/alpha for a one-span step).  step_dz / step_gamma_eff
+ * may be NULL; otherwise they receive n_steps values.
+ */
+int dbp_plan_describe(const dbp_link *link, const dbp_signal *signal, const dbp_steps *steps,
+                      dbp_plan_info *info, double *step_dz, double *step_gamma_eff);
+
+/*
+ * Creates a plan on the current CUDA device: validates the parameters, computes the
+ * step table, and builds on the GPU, in FP64, the dispersion transfer functions
+ * H_s(f_k) = exp(+j 2 pi^2 beta2 f_k^2 dz_s) / N (inverse of Eq. 1, phase reduced mod
+ * 2 pi before rounding to FP32) and the FFT twiddles; uploads gamma_eff_s * c_{s,i}.
+ * Synchronizes the legacy default stream before returning.  *out is owned by the
+ * caller and released with dbp_destroy.
+ */
+int dbp_plan(const dbp_link *link, const dbp_signal *signal, const dbp_steps *steps,
+             dbp_plan_t **out);
+
+/* Geometry of an existing plan. */
+int dbp_plan_get_info(const dbp_plan_t *plan, dbp_plan_info *info);
+
+/*
+ * Replaces the ESSFM coefficients (host array laid out as dbp_steps.coeffs, with the
+ * plan's coeffs_per_step).  Takes effect for work enqueued after the call; the upload
+ * is synchronous.
+ */
+int dbp_set_coeffs(dbp_plan_t *plan, const float *host_coeffs);
+
+/*
+ * Backpropagates n_waveforms waveforms: in and out are DEVICE pointers to
+ * complex64 [n_waveforms][2][n_samples]; out must not overlap in (DBP_ERR_ALIAS).
+ * One fused kernel per call: each thread block takes one overlap-save block of N
+ * vector samples and runs all N_s steps (FFT, x H_s, IFFT, nonlinear sub-step) in
+ * shared memory, writing its N - O central samples.  Asynchronous on `stream`.
+ */
+int dbp_run(dbp_plan_t *plan, const void *in, void *out, dbp_stream_t stream);
+
+/*
+ * As dbp_run, but in and out are HOST pointers (pinned or pageable).  The plan
+ * stages the data through device buffers it allocates on first use; copies and
+ * compute are pipelined over chunks of waveforms.  Returns after the result is in
+ * `out` (synchronizes `stream`).
+ */
+int dbp_run_host(dbp_plan_t *plan, const void *in, void *out, dbp_stream_t stream);
+
+/* Frees the plan's device tables and scratch (synchronizes the device first). */
+void dbp_destroy(dbp_plan_t *plan);
+
+/* Static description of an error code. */
+const char *dbp_strerror(int code);
+
+/* Library version string. */
+const char *dbp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DBP_H */

@@ -1,0 +1,8 @@
+// Forward DBP kernels for block length N = 8192 (ESSFM and SSFM variants).
+#include "fwd_kernel.cuh"
+
+namespace dbp {
+int launch_fwd_8192(const FwdParams &p, int n_wave, bool essfm, cudaStream_t st) {
+    return launch_fwd_n<8192>(p, n_wave, essfm, st);
+}
+}  // namespace dbp

@@ -1,0 +1,170 @@
+"""Python front end of libdbp: plans and runs digital backpropagation on the GPU.
+
+A ``Plan`` holds the link, signal and step parameters of Section II / III of
+arXiv:1507.00921 (SSFM with N_s steps, or ESSFM with N_c filter coefficients) and the
+device tables libdbp builds for them.  ``Plan.run`` takes a CUDA complex64 tensor
+[n_waveforms, 2, n_samples] (or [2, n_samples]) and returns the backpropagated field;
+every arithmetic step runs in libdbp's kernels on the tensor's device, on PyTorch's
+current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+
+_BOUNDARY = {"periodic": _lib.DBP_PERIODIC, "zero": _lib.DBP_ZERO}
+_METHOD = {"ssfm": _lib.DBP_SSFM, "essfm": _lib.DBP_ESSFM}
+
+
+def _link_struct(link: dict) -> _lib.dbp_link:
+    return _lib.dbp_link(int(link["n_spans"]), float(link["span_len_m"]), float(link["alpha_db_per_km"]),
+                         float(link["D_ps_per_nm_km"]), float(link["lambda_m"]), float(link["gamma_per_W_km"]),
+                         float(link.get("manakov_factor", 1.0)))
+
+
+@dataclass
+class PlanInfo:
+    fft_size: int
+    overlap: int
+    valid: int
+    n_blocks: int
+    n_steps: int
+    n_taps: int
+    beta2: float
+    memory: float
+    link_len_m: float
+    step_dz: np.ndarray
+    step_gamma_eff: np.ndarray
+
+
+class _Args:
+    """ctypes argument structs plus the host arrays they point into (kept alive)."""
+
+    def __init__(self, link, fs, n_samples, n_waveforms, boundary, method, n_steps, n_taps, coeffs,
+                 coeffs_per_step, step_len_m, gamma_eff, fft_size, overlap):
+        self.link = _link_struct(link)
+        self.signal = _lib.dbp_signal(float(fs), int(n_samples), int(n_waveforms), _BOUNDARY[boundary])
+        self.coeffs = None if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float32)
+        self.step_len = None if step_len_m is None else np.ascontiguousarray(step_len_m, dtype=np.float64)
+        self.gamma_eff = None if gamma_eff is None else np.ascontiguousarray(gamma_eff, dtype=np.float64)
+        fp = C.POINTER(C.c_float)
+        dp = C.POINTER(C.c_double)
+        self.steps = _lib.dbp_steps(
+            _METHOD[method], int(n_steps), int(n_taps),
+            self.coeffs.ctypes.data_as(fp) if self.coeffs is not None else fp(),
+            int(bool(coeffs_per_step)),
+            self.step_len.ctypes.data_as(dp) if self.step_len is not None else dp(),
+            self.gamma_eff.ctypes.data_as(dp) if self.gamma_eff is not None else dp(),
+            int(fft_size), int(overlap), _lib.DBP_FP32)
+
+
+def describe(link: dict, fs: float, n_samples: int, *, n_waveforms=1, boundary="periodic", method="essfm",
+             n_steps=1, n_taps=0, coeffs=None, coeffs_per_step=False, step_len_m=None, gamma_eff=None,
+             fft_size=4096, overlap=0) -> PlanInfo:
+    """Plan geometry and step table, computed by libdbp on the host (no GPU needed)."""
+    lib = _lib.load()
+    a = _Args(link, fs, n_samples, n_waveforms, boundary, method, n_steps, n_taps, coeffs, coeffs_per_step,
+              step_len_m, gamma_eff, fft_size, overlap)
+    info = _lib.dbp_plan_info()
+    dz = np.zeros(n_steps)
+    ge = np.zeros(n_steps)
+    dp = C.POINTER(C.c_double)
+    rc = lib.dbp_plan_describe(C.byref(a.link), C.byref(a.signal), C.byref(a.steps), C.byref(info),
+                               dz.ctypes.data_as(dp), ge.ctypes.data_as(dp))
+    _lib.check(rc, "dbp_plan_describe")
+    return PlanInfo(info.fft_size, info.overlap, info.valid, info.n_blocks, info.n_steps, info.n_taps,
+                    info.beta2_s2_per_m, info.memory_samples, info.link_len_m, dz, ge)
+
+
+class Plan:
+    """A libdbp plan on the current CUDA device."""
+
+    def __init__(self, link: dict, fs: float, n_samples: int, *, n_waveforms=1, boundary="periodic",
+                 method="essfm", n_steps=1, n_taps=0, coeffs=None, coeffs_per_step=False, step_len_m=None,
+                 gamma_eff=None, fft_size=4096, overlap=0):
+        import torch
+        self._lib = _lib.load()
+        self._args = _Args(link, fs, n_samples, n_waveforms, boundary, method, n_steps, n_taps, coeffs,
+                           coeffs_per_step, step_len_m, gamma_eff, fft_size, overlap)
+        self.n_samples = int(n_samples)
+        self.n_waveforms = int(n_waveforms)
+        self.method = method
+        self.coeffs_per_step = bool(coeffs_per_step)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.info = describe(link, fs, n_samples, n_waveforms=n_waveforms, boundary=boundary, method=method,
+                             n_steps=n_steps, n_taps=n_taps, coeffs=coeffs, coeffs_per_step=coeffs_per_step,
+                             step_len_m=step_len_m, gamma_eff=gamma_eff, fft_size=fft_size, overlap=overlap)
+        h = C.c_void_p()
+        rc = self._lib.dbp_plan(C.byref(self._args.link), C.byref(self._args.signal), C.byref(self._args.steps),
+                                C.byref(h))
+        _lib.check(rc, "dbp_plan")
+        self._h = h
+
+    # ------------------------------------------------------------------ helpers
+    def _check_tensor(self, x, name):
+        import torch
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.complex64:
+            raise TypeError(f"{name} must be a CUDA complex64 tensor")
+        if x.device != self.device:
+            raise ValueError(f"{name} is on {x.device}, plan on {self.device}")
+        want = (self.n_waveforms, 2, self.n_samples)
+        if x.numel() != np.prod(want) or x.shape[-2:] != (2, self.n_samples):
+            raise ValueError(f"{name} must have shape {want} (or [2, n] for one waveform)")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+
+    def run(self, x, out=None, stream=None):
+        """Backpropagate x (CUDA complex64 [n_waveforms, 2, n]); returns ``out``."""
+        import torch
+        self._check_tensor(x, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        else:
+            self._check_tensor(out, "out")
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        rc = self._lib.dbp_run(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                               C.c_void_p(st.cuda_stream))
+        _lib.check(rc, "dbp_run")
+        return out
+
+    def run_host(self, x, out=None, stream=None):
+        """Backpropagate a HOST complex64 array/tensor; copies in and out inside libdbp."""
+        import torch
+        xt = torch.as_tensor(x)
+        if xt.is_cuda or xt.dtype != torch.complex64 or not xt.is_contiguous():
+            raise TypeError("x must be a contiguous host complex64 array")
+        if xt.numel() != self.n_waveforms * 2 * self.n_samples:
+            raise ValueError("x has the wrong number of samples")
+        if out is None:
+            out = torch.empty(xt.shape, dtype=torch.complex64, pin_memory=xt.is_pinned())
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        rc = self._lib.dbp_run_host(self._h, C.c_void_p(xt.data_ptr()), C.c_void_p(out.data_ptr()),
+                                    C.c_void_p(st.cuda_stream))
+        _lib.check(rc, "dbp_run_host")
+        return out
+
+    def set_coeffs(self, coeffs):
+        c = np.ascontiguousarray(coeffs, dtype=np.float32)
+        rc = self._lib.dbp_set_coeffs(self._h, c.ctypes.data_as(C.POINTER(C.c_float)))
+        _lib.check(rc, "dbp_set_coeffs")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.dbp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
