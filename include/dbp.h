@@ -161,6 +161,14 @@ const char *dbp_strerror(int code);
 /* Library version string. */
 const char *dbp_version(void);
 
+/*
+ * Diagnostic (no counterpart in the paper): launches n_blocks x 256 threads that each
+ * run iters x 128 independent FP32 FMAs (256 flop), for measuring the FP32-pipe peak the
+ * DBP kernels are compared against.  `out` is a device buffer of n_blocks * 256 floats
+ * that is normally left untouched.  Asynchronous on `stream`.
+ */
+int dbp_diag_fma(void *out, int n_blocks, int iters, dbp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

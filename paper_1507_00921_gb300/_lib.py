@@ -71,6 +71,7 @@ _PROTOS = {
     "dbp_destroy": (None, [_P]),
     "dbp_strerror": (C.c_char_p, [C.c_int]),
     "dbp_version": (C.c_char_p, []),
+    "dbp_diag_fma": (C.c_int, [_P, C.c_int, C.c_int, _P]),
 }
 
 _lib = None

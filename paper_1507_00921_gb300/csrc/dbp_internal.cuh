@@ -10,6 +10,11 @@ namespace dbp {
 // Three-pass FFT geometry N = N2 * N1 * N0 (passes in that order, strides N0*N1, N0, 1).
 // The last pass (radix N0) is contiguous; its output sits at the digit-reversed position
 // p = k2 + N0 k1 + N0 N1 k0 of frequency k = k0 + N2 k1 + N2 N1 k2.
+// Shared memory (bytes): the block with both polarizations interleaved, one float4
+// (x_pol0, x_pol1) per position plus one float4 of padding per N0 positions; the step's
+// H table; the split first-pass twiddles W_N^{c k} = A[c mod 16][k] * B[c div 16][k];
+// the second-pass twiddles.  The ESSFM intensity P and phase theta arrays reuse the
+// block buffer while the block is held in registers.
 template <int N>
 struct Geo {
     static constexpr int N0 = (N >= 8192) ? 32 : 16;
@@ -17,11 +22,20 @@ struct Geo {
     static constexpr int N2 = N / (N0 * N1);
     static constexpr int T = N / 16;                 // threads per CTA
     static constexpr int S1 = N0 * N1;               // stride of the first pass
-    static constexpr int PADN = N + 2 * (N / N0);    // float2 per polarization (+16 B per N0)
+    static constexpr int PADX = N + N / N0;          // float4 slots of the block buffer
     static constexpr int PADP = N + 4 * (N / 16);    // floats of P / theta (+16 B per 16)
+    static constexpr int PADH = N + 2 * (N / N0);    // float2 of the H table (+16 B per N0)
+    static constexpr int TWA = 16 * N2;
+    static constexpr int TWB = (S1 / 16) * N2;
+    static constexpr int TW2 = N0 * N1;
+    static constexpr size_t OFF_H = (size_t)PADX * 16;
+    static constexpr size_t OFF_TWA = OFF_H + (size_t)PADH * 8;
+    static constexpr size_t OFF_TWB = OFF_TWA + (size_t)TWA * 8;
+    static constexpr size_t OFF_TW2 = OFF_TWB + (size_t)TWB * 8;
+    static constexpr size_t SMEM = OFF_TW2 + (size_t)TW2 * 8;
     static constexpr int MINB = (512 / T) > 0 ? (512 / T) : 1;
-    static constexpr size_t SMEM_SSFM = (size_t)2 * PADN * sizeof(float2);
-    static constexpr size_t SMEM_ESSFM = SMEM_SSFM + (size_t)2 * PADP * sizeof(float);
+    static_assert(2 * PADP * 4 <= PADX * 16, "P/theta must fit in the block buffer");
+    static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
 
 inline void host_geo(int n, int &n0, int &n1, int &n2) {
@@ -47,7 +61,8 @@ struct FwdParams {
     long long h_stride;     // float2 between consecutive steps' H tables (0: shared)
     const float2 *H;        // [steps][N] H_s / N at digit-reversed positions
     const float *taps;      // [steps][taps_stride]: gamma_eff_s * c_{s,i}, zero padded
-    const float2 *tw1;      // [N0 N1][N2] W_N^{c k}
+    const float2 *twA;      // [16][N2] W_N^{cl k}
+    const float2 *twB;      // [N0 N1 / 16][N2] W_{N/16}^{ch k}
     const float2 *tw2;      // [N0][N1] W_{N0 N1}^{n0 k1}
 };
 
@@ -64,7 +79,8 @@ struct PlanImpl {
     // device tables
     float2 *d_H = nullptr;
     float *d_taps = nullptr;
-    float2 *d_tw1 = nullptr;
+    float2 *d_twA = nullptr;
+    float2 *d_twB = nullptr;
     float2 *d_tw2 = nullptr;
     // host copies
     double *step_dz = nullptr;

@@ -11,7 +11,8 @@
 // Tables built on the GPU in FP64 and rounded once to FP32:
 //   H_s at digit-reversed position p: exp(+j 2 pi^2 beta2 f_k^2 dz_s) / N, with the
 //   phase reduced modulo 2 pi in FP64 first (it reaches ~10^3 rad over 3200 km);
-//   FFT twiddles W_N^{c k} and W_{N0 N1}^{n0 k1}.
+//   FFT twiddles W_N^{c k} (split as W_N^{(c mod 16) k} W_{N/16}^{(c div 16) k}) and
+//   W_{N0 N1}^{n0 k1}.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -45,20 +46,23 @@ __global__ void build_h_kernel(float2 *H, int N, int n0, int n1, int n2, double 
     H[(size_t)tbl * N + pidx] = make_float2((float)(c / N), (float)(s / N));
 }
 
-__global__ void build_twiddle_kernel(float2 *tw1, float2 *tw2, int N, int n0, int n1, int n2) {
+__global__ void build_twiddle_kernel(float2 *twA, float2 *twB, float2 *tw2, int N, int n0, int n1, int n2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) {                        // tw1[c][k] = exp(-j 2 pi c k / N), c < n0 n1, k < n2
-        const int c = i / n2, k = i % n2;
-        const long long m = ((long long)c * k) % N;
-        double s, co;
+    double s, co;
+    if (i < 16 * n2) {                  // A[cl][k] = exp(-j 2 pi cl k / N), cl < 16
+        const int cl = i / n2, k = i % n2;
+        sincospi(-2.0 * (double)((cl * k) % N) / (double)N, &s, &co);
+        twA[i] = make_float2((float)co, (float)s);
+    }
+    if (i < (n0 * n1 / 16) * n2) {      // B[ch][k] = exp(-j 2 pi 16 ch k / N), ch < n0 n1 / 16
+        const int ch = i / n2, k = i % n2;
+        const long long m = (16LL * ch * k) % N;
         sincospi(-2.0 * (double)m / (double)N, &s, &co);
-        tw1[i] = make_float2((float)co, (float)s);
+        twB[i] = make_float2((float)co, (float)s);
     }
     if (i < n0 * n1) {                  // tw2[n0][k1] = exp(-j 2 pi n0 k1 / (n0 n1))
         const int a = i / n1, k = i % n1;
-        const int m = (a * k) % (n0 * n1);
-        double s, co;
-        sincospi(-2.0 * (double)m / (double)(n0 * n1), &s, &co);
+        sincospi(-2.0 * (double)((a * k) % (n0 * n1)) / (double)(n0 * n1), &s, &co);
         tw2[i] = make_float2((float)co, (float)s);
     }
 }
@@ -179,7 +183,8 @@ static int upload_taps(PlanImpl &P, const float *host_coeffs) {
 static void release(PlanImpl &P) {
     if (P.d_H) cudaFree(P.d_H);
     if (P.d_taps) cudaFree(P.d_taps);
-    if (P.d_tw1) cudaFree(P.d_tw1);
+    if (P.d_twA) cudaFree(P.d_twA);
+    if (P.d_twB) cudaFree(P.d_twB);
     if (P.d_tw2) cudaFree(P.d_tw2);
     if (P.d_stage_in) cudaFree(P.d_stage_in);
     if (P.d_stage_out) cudaFree(P.d_stage_out);
@@ -240,7 +245,8 @@ static int make_plan(const dbp_link *link, const dbp_signal *sig, const dbp_step
     double *d_dz = nullptr;
     rc = dev_alloc((void **)&P.d_H, sizeof(float2) * (size_t)N * n_tables);
     if (!rc) rc = dev_alloc((void **)&P.d_taps, sizeof(float) * (size_t)ns * P.taps_stride);
-    if (!rc) rc = dev_alloc((void **)&P.d_tw1, sizeof(float2) * (size_t)N);
+    if (!rc) rc = dev_alloc((void **)&P.d_twA, sizeof(float2) * (size_t)16 * n2);
+    if (!rc) rc = dev_alloc((void **)&P.d_twB, sizeof(float2) * (size_t)(n0 * n1 / 16) * n2);
     if (!rc) rc = dev_alloc((void **)&P.d_tw2, sizeof(float2) * (size_t)n0 * n1);
     if (!rc) rc = dev_alloc((void **)&d_dz, sizeof(double) * n_tables);
     if (!rc && cudaMemcpy(d_dz, P.step_dz, sizeof(double) * n_tables, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -248,7 +254,7 @@ static int make_plan(const dbp_link *link, const dbp_signal *sig, const dbp_step
     if (!rc) {
         dim3 g((N + 255) / 256, n_tables);
         build_h_kernel<<<g, 256>>>(P.d_H, N, n0, n1, n2, info.beta2_s2_per_m, sig->sample_rate_hz, d_dz, n_tables);
-        build_twiddle_kernel<<<(N + 255) / 256, 256>>>(P.d_tw1, P.d_tw2, N, n0, n1, n2);
+        build_twiddle_kernel<<<(N + 255) / 256, 256>>>(P.d_twA, P.d_twB, P.d_tw2, N, n0, n1, n2);
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) rc = DBP_ERR_CUDA;
     }
     if (d_dz) cudaFree(d_dz);
@@ -282,7 +288,8 @@ static int launch(const PlanImpl &P, const void *in, void *out, int n_wave, cuda
     p.h_stride = P.h_shared ? 0 : P.info.fft_size;
     p.H = P.d_H;
     p.taps = P.d_taps;
-    p.tw1 = P.d_tw1;
+    p.twA = P.d_twA;
+    p.twB = P.d_twB;
     p.tw2 = P.d_tw2;
     const bool essfm = P.method == DBP_ESSFM;
     switch (P.info.fft_size) {

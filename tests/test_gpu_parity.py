@@ -86,6 +86,7 @@ def test_parity_with_oracle(torch_cuda, case):
     cfg = oracle_cfg(link, kw, info)
     ref = odbp.dbp(x.astype(np.complex64).astype(np.complex128), cfg)
     rel_rms, max_rel = compare(got, ref)
+    print(f"\n{name}: relative RMS error {rel_rms:.3e}, max error / RMS {max_rel:.3e}")
     assert rel_rms <= TOL_RMS, (rel_rms, max_rel)
     assert max_rel <= TOL_MAX, (rel_rms, max_rel)
 
