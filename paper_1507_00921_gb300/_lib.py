@@ -20,6 +20,9 @@ DBP_ERR_CUDA = -4
 DBP_ERR_TIMEOUT = -5
 DBP_ERR_ALIAS = -6
 DBP_ERR_UNSUPPORTED = -7
+DBP_ERR_SCRATCH = -8
+DBP_NOALLOC_SCRATCH_BYTES = 1 << 20
+DBP_NOALLOC_MAX_STEPS = 64
 
 DBP_PERIODIC, DBP_ZERO = 0, 1
 DBP_SSFM, DBP_ESSFM = 0, 1
@@ -68,6 +71,7 @@ _PROTOS = {
     "dbp_set_coeffs": (C.c_int, [_P, C.POINTER(C.c_float)]),
     "dbp_run": (C.c_int, [_P, _P, _P, _P]),
     "dbp_run_host": (C.c_int, [_P, _P, _P, _P]),
+    "dbp_run_noalloc": (C.c_int, [C.POINTER(dbp_link), C.POINTER(dbp_signal), C.POINTER(dbp_steps), _P, _P, _P]),
     "dbp_destroy": (None, [_P]),
     "dbp_strerror": (C.c_char_p, [C.c_int]),
     "dbp_version": (C.c_char_p, []),

@@ -93,6 +93,15 @@ struct PlanImpl {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
 };
 
+// Planner pieces shared by the entry points (plan.cu).
+int describe(const dbp_link *link, const dbp_signal *sig, const dbp_steps *st, dbp_plan_info *info, double *dz,
+             double *geff);
+bool overlaps(const void *a, const void *b, size_t bytes);
+int launch(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_t st);
+__global__ void build_h_kernel(float2 *H, int N, int n0, int n1, int n2, double beta2, double fs, const double *dz,
+                               int n_tables);
+__global__ void build_twiddle_kernel(float2 *twA, float2 *twB, float2 *tw2, int N, int n0, int n1, int n2);
+
 // Kernel launchers (one translation unit per block length).
 int launch_fwd_512(const FwdParams &, int n_wave, bool essfm, cudaStream_t);
 int launch_fwd_1024(const FwdParams &, int n_wave, bool essfm, cudaStream_t);

@@ -119,7 +119,7 @@ static int validate(const dbp_link *link, const dbp_signal *sig, const dbp_steps
     return DBP_OK;
 }
 
-static int describe(const dbp_link *link, const dbp_signal *sig, const dbp_steps *st, dbp_plan_info *info,
+int describe(const dbp_link *link, const dbp_signal *sig, const dbp_steps *st, dbp_plan_info *info,
                     double *dz, double *geff) {
     int rc = validate(link, sig, st);
     if (rc) return rc;
@@ -268,12 +268,12 @@ static int make_plan(const dbp_link *link, const dbp_signal *sig, const dbp_step
     return DBP_OK;
 }
 
-static bool overlaps(const void *a, const void *b, size_t bytes) {
+bool overlaps(const void *a, const void *b, size_t bytes) {
     const char *x = (const char *)a, *y = (const char *)b;
     return x < y + bytes && y < x + bytes;
 }
 
-static int launch(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_t st) {
+int launch(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_t st) {
     FwdParams p;
     p.in = (const float2 *)in;
     p.out = (float2 *)out;
@@ -412,6 +412,7 @@ const char *dbp_strerror(int code) {
         case DBP_ERR_TIMEOUT: return "bounded device wait timed out";
         case DBP_ERR_ALIAS: return "output buffer overlaps input buffer";
         case DBP_ERR_UNSUPPORTED: return "unsupported option";
+        case DBP_ERR_SCRATCH: return "problem exceeds the fixed scratch of dbp_run_noalloc";
         default: return "unknown error";
     }
 }

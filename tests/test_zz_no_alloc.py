@@ -1,0 +1,76 @@
+"""dbp_run_noalloc: the entry point for callers that cannot allocate device memory
+(for example code running while a CUDA graph is being built, or a host that must stay
+within pre-reserved buffers).  It must give what dbp_plan + dbp_run give, on
+consecutive calls that reuse its one fixed scratch area, and refuse problems that do
+not fit that scratch.  Called through the C ABI with ctypes."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import synth
+from paper_1507_00921_gb300 import _lib
+from paper_1507_00921_gb300.dbp import _Args
+
+FS = synth.SAMPLE_RATE
+TOL_RMS = 1e-5          # the parity tolerance of the FP32 path
+
+
+def _args(spans, n, nw, **kw):
+    kw.setdefault("coeffs", None)
+    return _Args(synth.link(spans), FS, n, nw, kw.pop("boundary", "periodic"), kw.pop("method"),
+                 kw.pop("n_steps"), kw.pop("n_taps", 0), kw.pop("coeffs"), kw.pop("coeffs_per_step", False),
+                 kw.pop("step_len_m", None), kw.pop("gamma_eff", None), kw.pop("fft_size"), kw.pop("overlap", 0))
+
+
+def _noalloc(lib, a, x_ptr, y_ptr, stream=0):
+    return lib.dbp_run_noalloc(C.byref(a.link), C.byref(a.signal), C.byref(a.steps), C.c_void_p(x_ptr),
+                               C.c_void_p(y_ptr), C.c_void_p(stream))
+
+
+def test_noalloc_rejects_problems_beyond_its_scratch():
+    lib = _lib.load()
+    x = C.c_void_p(16)
+    y = C.c_void_p(1 << 40)
+    too_many = _args(40, 4096, 1, method="ssfm", n_steps=_lib.DBP_NOALLOC_MAX_STEPS + 1, fft_size=8192)
+    assert lib.dbp_run_noalloc(C.byref(too_many.link), C.byref(too_many.signal), C.byref(too_many.steps), x, y,
+                               None) == _lib.DBP_ERR_SCRATCH
+    dz = np.linspace(0.5, 1.5, 20)
+    dz = dz / dz.sum() * 3.2e6                      # 20 distinct step lengths: 20 H tables at N = 8192
+    big = _args(40, 4096, 1, method="ssfm", n_steps=20, step_len_m=dz, fft_size=8192)
+    assert lib.dbp_run_noalloc(C.byref(big.link), C.byref(big.signal), C.byref(big.steps), x, y,
+                               None) == _lib.DBP_ERR_SCRATCH
+    assert lib.dbp_strerror(_lib.DBP_ERR_SCRATCH) != b"unknown error"
+    assert lib.dbp_run_noalloc(None, None, None, None, None, None) == _lib.DBP_ERR_ARG
+
+
+@pytest.mark.gpu
+def test_noalloc_matches_planned_run_on_consecutive_calls():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_00921_gb300 import Plan
+    lib = _lib.load()
+    c32 = 0.6 * np.exp(-np.arange(33) / 10.0)
+    c32 = (c32 / (c32[0] + 2 * c32[1:].sum())).astype(np.float32)
+    calls = [
+        (40, 3 * 6760 + 11, 2, dict(method="essfm", n_steps=1, n_taps=32, coeffs=c32, fft_size=8192)),
+        (10, 20000, 3, dict(method="ssfm", n_steps=5, fft_size=2048, boundary="zero")),
+        (40, 12000, 1, dict(method="essfm", n_steps=3, n_taps=4, fft_size=4096,
+                            step_len_m=np.array([0.5e6, 1.2e6, 1.5e6]),
+                            coeffs=np.array([0.5, 0.2, 0.05, 0.01, 0.0], dtype=np.float32))),
+    ]
+    stream = torch.cuda.current_stream()
+    for spans, n, nw, kw in calls:
+        x = torch.from_numpy(synth.random_field(nw, n, synth.dbm_to_w(2.0), seed=n).astype(np.complex64)).cuda()
+        a = _args(spans, n, nw, **dict(kw))
+        y = torch.empty_like(x)
+        rc = _noalloc(lib, a, x.data_ptr(), y.data_ptr(), stream.cuda_stream)
+        assert rc == _lib.DBP_OK, lib.dbp_strerror(rc)
+        kw2 = dict(kw)
+        with Plan(synth.link(spans), FS, n, n_waveforms=nw, **kw2) as plan:
+            ref = plan.run(x)
+        torch.cuda.synchronize()
+        got, want = y.cpu().numpy(), ref.cpu().numpy()
+        rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert rel <= TOL_RMS, rel
