@@ -61,9 +61,9 @@ struct FwdParams {
     long long h_stride;     // float2 between consecutive steps' H tables (0: shared)
     const float2 *H;        // [steps][N] H_s / N at digit-reversed positions
     const float *taps;      // [steps][taps_stride]: gamma_eff_s * c_{s,i}, zero padded
-    const float2 *twA;      // [16][N2] W_N^{cl k}
-    const float2 *twB;      // [N0 N1 / 16][N2] W_{N/16}^{ch k}
-    const float2 *tw2;      // [N0][N1] W_{N0 N1}^{n0 k1}
+    const float2 *twA;      // [N2][16] W_N^{cl k}
+    const float2 *twB;      // [N2][N0 N1 / 16] W_{N/16}^{ch k}
+    const float2 *tw2;      // [N1][N0] W_{N0 N1}^{n0 k1}
 };
 
 struct PlanImpl {

@@ -157,13 +157,13 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
 #pragma unroll
         for (int i = 0; i < C1; ++i) {
             const int c = t + T * i;
-            const float2 *ta = sA + (c & 15) * N2;
-            const float2 *tb = sB + (c >> 4) * N2;
+            const float2 *ta = sA + (c & 15);
+            const float2 *tb = sB + (c >> 4);
             Dft<N2, false>::run(v[0][i]);
             Dft<N2, false>::run(v[1][i]);
 #pragma unroll
             for (int k = 1; k < N2; ++k) {
-                const float2 wk = cmul(ta[k], tb[k]);
+                const float2 wk = cmul(ta[16 * k], tb[(S1 / 16) * k]);
                 v[0][i][k] = cmul(v[0][i][k], wk);
                 v[1][i][k] = cmul(v[1][i][k], wk);
             }
@@ -188,10 +188,10 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
             }
             Dft<N1, false>::run(u0);
             Dft<N1, false>::run(u1);
-            const float2 *tw = s2 + n0 * N1;
+            const float2 *tw = s2 + n0;
 #pragma unroll
             for (int k = 1; k < N1; ++k) {
-                const float2 wk = tw[k];
+                const float2 wk = tw[N0 * k];
                 u0[k] = cmul(u0[k], wk);
                 u1[k] = cmul(u1[k], wk);
             }
@@ -214,12 +214,14 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
             }
             Dft<16, false>::run(u0);
             Dft<16, false>::run(u1);
-            const float2 *hrow = sH + hphys<16>(base);
+            const float4 *hrow = reinterpret_cast<const float4 *>(sH + hphys<16>(base));
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float2 h = hrow[j];
-                u0[j] = cmul(u0[j], h);
-                u1[j] = cmul(u1[j], h);
+            for (int j = 0; j < 8; ++j) {
+                const float4 h = hrow[j];
+                u0[2 * j] = cmul(u0[2 * j], make_float2(h.x, h.y));
+                u1[2 * j] = cmul(u1[2 * j], make_float2(h.x, h.y));
+                u0[2 * j + 1] = cmul(u0[2 * j + 1], make_float2(h.z, h.w));
+                u1[2 * j + 1] = cmul(u1[2 * j + 1], make_float2(h.z, h.w));
             }
             Dft<16, true>::run(u0);
             Dft<16, true>::run(u1);
@@ -233,9 +235,13 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
 #pragma unroll
             for (int j = 0; j < N0; ++j) u[j] = xh[2 * xphys<N0>(base + j) + pol];
             Dft<N0, false>::run(u);
-            const float2 *hrow = sH + hphys<N0>(base);
+            const float4 *hrow = reinterpret_cast<const float4 *>(sH + hphys<N0>(base));
 #pragma unroll
-            for (int j = 0; j < N0; ++j) u[j] = cmul(u[j], hrow[j]);
+            for (int j = 0; j < N0 / 2; ++j) {
+                const float4 h = hrow[j];
+                u[2 * j] = cmul(u[2 * j], make_float2(h.x, h.y));
+                u[2 * j + 1] = cmul(u[2 * j + 1], make_float2(h.z, h.w));
+            }
             Dft<N0, true>::run(u);
 #pragma unroll
             for (int j = 0; j < N0; ++j) xh[2 * xphys<N0>(base + j) + pol] = u[j];
@@ -256,10 +262,10 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
                 u0[j] = make_float2(f.x, f.y);
                 u1[j] = make_float2(f.z, f.w);
             }
-            const float2 *tw = s2 + n0 * N1;
+            const float2 *tw = s2 + n0;
 #pragma unroll
             for (int k = 1; k < N1; ++k) {
-                const float2 wk = tw[k];
+                const float2 wk = tw[N0 * k];
                 u0[k] = cmulc(u0[k], wk);
                 u1[k] = cmulc(u1[k], wk);
             }
@@ -275,8 +281,8 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
 #pragma unroll
         for (int i = 0; i < C1; ++i) {
             const int c = t + T * i;
-            const float2 *ta = sA + (c & 15) * N2;
-            const float2 *tb = sB + (c >> 4) * N2;
+            const float2 *ta = sA + (c & 15);
+            const float2 *tb = sB + (c >> 4);
 #pragma unroll
             for (int j = 0; j < N2; ++j) {
                 const float4 f = xs[xphys<N0>(c + S1 * j)];
@@ -285,7 +291,7 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
             }
 #pragma unroll
             for (int k = 1; k < N2; ++k) {
-                const float2 wk = cmul(ta[k], tb[k]);
+                const float2 wk = cmul(ta[16 * k], tb[(S1 / 16) * k]);
                 v[0][i][k] = cmulc(v[0][i][k], wk);
                 v[1][i][k] = cmulc(v[1][i][k], wk);
             }

@@ -46,22 +46,25 @@ __global__ void build_h_kernel(float2 *H, int N, int n0, int n1, int n2, double 
     H[(size_t)tbl * N + pidx] = make_float2((float)(c / N), (float)(s / N));
 }
 
+// Twiddle tables, stored k-major so that lanes reading consecutive rows for one k hit
+// consecutive shared-memory banks.
 __global__ void build_twiddle_kernel(float2 *twA, float2 *twB, float2 *tw2, int N, int n0, int n1, int n2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double s, co;
-    if (i < 16 * n2) {                  // A[cl][k] = exp(-j 2 pi cl k / N), cl < 16
-        const int cl = i / n2, k = i % n2;
+    if (i < 16 * n2) {                  // A[k][cl] = exp(-j 2 pi cl k / N), cl < 16
+        const int k = i / 16, cl = i % 16;
         sincospi(-2.0 * (double)((cl * k) % N) / (double)N, &s, &co);
         twA[i] = make_float2((float)co, (float)s);
     }
-    if (i < (n0 * n1 / 16) * n2) {      // B[ch][k] = exp(-j 2 pi 16 ch k / N), ch < n0 n1 / 16
-        const int ch = i / n2, k = i % n2;
+    const int nb = n0 * n1 / 16;
+    if (i < nb * n2) {                  // B[k][ch] = exp(-j 2 pi 16 ch k / N), ch < n0 n1 / 16
+        const int k = i / nb, ch = i % nb;
         const long long m = (16LL * ch * k) % N;
         sincospi(-2.0 * (double)m / (double)N, &s, &co);
         twB[i] = make_float2((float)co, (float)s);
     }
-    if (i < n0 * n1) {                  // tw2[n0][k1] = exp(-j 2 pi n0 k1 / (n0 n1))
-        const int a = i / n1, k = i % n1;
+    if (i < n0 * n1) {                  // W2[k1][a] = exp(-j 2 pi a k1 / (n0 n1)), a < n0
+        const int k = i / n0, a = i % n0;
         sincospi(-2.0 * (double)((a * k) % (n0 * n1)) / (double)(n0 * n1), &s, &co);
         tw2[i] = make_float2((float)co, (float)s);
     }
