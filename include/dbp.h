@@ -146,6 +146,31 @@ int dbp_set_coeffs(dbp_plan_t *plan, const float *host_coeffs);
 int dbp_run(dbp_plan_t *plan, const void *in, void *out, dbp_stream_t stream);
 
 /*
+ * Reverse-mode gradient of dbp_run (no counterpart in the paper's experiment, which fits
+ * the coefficients by MSE, Section IV; derived from Eqs. 1-3 and Section III).  For a
+ * real loss L with grad_out = dL/dRe(out) + j dL/dIm(out) (DEVICE complex64, same layout
+ * as out), writes (each pointer may be NULL to skip; values are overwritten):
+ *   grad_in      DEVICE complex64 [n_waveforms][2][n_samples]: dL/dRe(in) + j dL/dIm(in)
+ *   d_coeffs     DEVICE float: dL/dc_{s,i}, [n_steps][n_taps+1] if coeffs_per_step, else
+ *                [n_taps+1] summed over steps (c unscaled: theta = gamma_eff_s sum c_i S_i)
+ *   d_gamma_eff  DEVICE float [n_steps]: dL/dgamma_eff_s
+ *   d_step_len   DEVICE float [n_steps]: dL/ddz_s through H_s (gamma_eff_s held fixed)
+ * for the plan's current coefficients and steps, on `stream`.  The plan allocates its
+ * scratch (per-block gradients, spectra, step checkpoints, partial sums) on the first
+ * call.  Deterministic: no floating-point atomics.  grad_in must not overlap in or
+ * grad_out (DBP_ERR_ALIAS).
+ */
+int dbp_grad(dbp_plan_t *plan, const void *in, const void *grad_out, void *grad_in, float *d_coeffs,
+             float *d_gamma_eff, float *d_step_len, dbp_stream_t stream);
+
+/*
+ * Replaces the step lengths dz_s (host [n_steps], rebuilds H_s on the GPU in FP64) and/or
+ * the nonlinear strengths gamma_eff_s (host [n_steps]); NULL keeps the current values.
+ * The overlap and block geometry are not changed.  Synchronizes the device.
+ */
+int dbp_set_steps(dbp_plan_t *plan, const double *step_len_m, const double *gamma_eff);
+
+/*
  * As dbp_run, but in and out are HOST pointers (pinned or pageable).  The plan
  * stages the data through device buffers it allocates on first use; copies and
  * compute are pipelined over chunks of waveforms.  Returns after the result is in

@@ -71,6 +71,8 @@ _PROTOS = {
     "dbp_set_coeffs": (C.c_int, [_P, C.POINTER(C.c_float)]),
     "dbp_run": (C.c_int, [_P, _P, _P, _P]),
     "dbp_run_host": (C.c_int, [_P, _P, _P, _P]),
+    "dbp_grad": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "dbp_set_steps": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "dbp_run_noalloc": (C.c_int, [C.POINTER(dbp_link), C.POINTER(dbp_signal), C.POINTER(dbp_steps), _P, _P, _P]),
     "dbp_destroy": (None, [_P]),
     "dbp_strerror": (C.c_char_p, [C.c_int]),

@@ -1,0 +1,8 @@
+// Adjoint DBP kernels for block length N = 4096 (ESSFM and SSFM variants).
+#include "adj_kernel.cuh"
+
+namespace dbp {
+int launch_adj_4096(const AdjParams &q, int n_wave, bool essfm, cudaStream_t st) {
+    return launch_adj_n<4096>(q, n_wave, essfm, st);
+}
+}  // namespace dbp

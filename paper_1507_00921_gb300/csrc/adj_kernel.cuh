@@ -1,0 +1,383 @@
+// Adjoint (reverse mode) of the fused overlap-save DBP: gradients of a real loss with
+// respect to the input waveform, the ESSFM coefficients c_{s,i}, the per-step
+// nonlinear strengths gamma_eff_s and the step lengths dz_s (through H_s only).
+//
+// Gradient convention: g = dL/dRe + j dL/dIm.  Derived from the forward operators of
+// Section II (Eqs. 1-3) and Section III's overlap-and-save:
+//   nonlinear z = y exp(j theta), theta = gamma_eff sum_i c_i S_i (S_0 = P_k,
+//     S_i = P_{k-i} + P_{k+i}):  s_k = dL/dtheta_k = -sum_pol Im(conj(g_z) z);
+//     R_i = sum_k s_k S_{k,i} (dL/dc_i = gamma_eff R_i, dL/dgamma_eff = sum_i c_i R_i);
+//     dL/dP = the same symmetric filter applied to s;  g_y = g_z exp(-j theta) + 2 (dL/dP) y
+//   linear y = IDFT(H' DFT(x)), H' = H / N:  g_x = IDFT(conj(H') DFT(g_y));
+//     dL/ddz = sum_k phi'_k Re(j conj(G_k) U_k), G = DFT(g_y), U = H' DFT(x),
+//     phi'_k = 2 pi^2 beta2 f_k^2
+//   overlap-and-save transposes to overlap-add of the block input gradients.
+// One CTA per block: a forward sweep stores each step's input (checkpoints); the reverse
+// sweep recomputes each step's linear sub-step from its checkpoint.  Per-block partial
+// sums of R_i and dL/ddz go to scratch and are reduced in a fixed order, so the result
+// is bitwise reproducible.
+#pragma once
+#include "block_fft.cuh"
+
+namespace dbp {
+
+struct AdjParams {
+    FwdParams f;             // in = waveform x, plan tables
+    const float2 *gout;      // [n_wave][2][n] dL/d(out)
+    float4 *gblk;            // [blocks][N] block gradient (both polarizations per position)
+    float4 *uscr;            // [blocks][N] U = H' DFT(x) of the step being reversed
+    float4 *yscr;            // [blocks][N] y of the step being reversed
+    float4 *ckpt;            // [blocks][n_steps - 1][N] inputs of steps 1..n_steps-1
+    float *part;             // [blocks][n_steps * nr + n_steps]: R_{s,i} then dL/ddz_s
+    int nr;                  // correlations per step: 1 + 8 n_tapblk
+    float cphi;              // 2 pi^2 beta2 (f_s / N)^2
+};
+
+template <int N, int K>
+__device__ __forceinline__ void block_sum(float (&val)[K], float *red, float *dst, int t) {
+    constexpr int W = Geo<N>::T / 32;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float x = val[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        val[k] = x;
+    }
+    if ((t & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[(t >> 5) * K + k] = val[k];
+    }
+    __syncthreads();
+    if (t < K) {
+        float s = 0.f;
+        for (int w = 0; w < W; ++w) s += red[w * K + t];
+        dst[t] = s;
+    }
+    __syncthreads();
+}
+
+// pass-3 operation of the recomputed linear sub-step: x H_s, and keep U = H' X
+template <int N>
+struct MidRecompute {
+    const float2 *sH;
+    float4 *U;
+    __device__ __forceinline__ void two(float2 (&u0)[16], float2 (&u1)[16], int base) {
+        MidMulH<N>{sH}.two(u0, u1, base);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) U[base + j] = make_float4(u0[j].x, u0[j].y, u1[j].x, u1[j].y);
+    }
+    template <int R>
+    __device__ __forceinline__ void one(float2 (&u)[R], int pol, int base) {
+        MidMulH<N>{sH}.one(u, pol, base);
+        float2 *uh = reinterpret_cast<float2 *>(U);
+#pragma unroll
+        for (int j = 0; j < R; ++j) uh[2 * (base + j) + pol] = u[j];
+    }
+};
+
+// pass-3 operation of the linear adjoint: accumulate dL/ddz, then x conj(H_s)
+template <int N>
+struct MidAdjoint {
+    const float2 *sH;
+    const float4 *U;
+    float cphi;
+    float acc;
+    __device__ __forceinline__ float phi_prime(int p) const {
+        using G = Geo<N>;
+        const int k2 = p % G::N0, k1 = (p / G::N0) % G::N1, k0 = p / (G::N0 * G::N1);
+        int k = k0 + G::N2 * k1 + G::N2 * G::N1 * k2;
+        if (k >= N / 2) k -= N;
+        const float kk = (float)k;
+        return cphi * kk * kk;
+    }
+    __device__ __forceinline__ static float mimag(float2 g, float2 u) { return g.y * u.x - g.x * u.y; }  // -Im(conj(g) u)
+    __device__ __forceinline__ void two(float2 (&u0)[16], float2 (&u1)[16], int base) {
+        const float4 *hrow = reinterpret_cast<const float4 *>(sH + hphys<16>(base));
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float4 uu = U[base + j];
+            acc = fmaf(phi_prime(base + j),
+                       mimag(u0[j], make_float2(uu.x, uu.y)) + mimag(u1[j], make_float2(uu.z, uu.w)), acc);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 h = hrow[j];
+            u0[2 * j] = cmulc(u0[2 * j], make_float2(h.x, h.y));
+            u1[2 * j] = cmulc(u1[2 * j], make_float2(h.x, h.y));
+            u0[2 * j + 1] = cmulc(u0[2 * j + 1], make_float2(h.z, h.w));
+            u1[2 * j + 1] = cmulc(u1[2 * j + 1], make_float2(h.z, h.w));
+        }
+    }
+    template <int R>
+    __device__ __forceinline__ void one(float2 (&u)[R], int pol, int base) {
+        const float2 *uh = reinterpret_cast<const float2 *>(U);
+        const float4 *hrow = reinterpret_cast<const float4 *>(sH + hphys<R>(base));
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc = fmaf(phi_prime(base + j), mimag(u[j], uh[2 * (base + j) + pol]), acc);
+#pragma unroll
+        for (int j = 0; j < R / 2; ++j) {
+            const float4 h = hrow[j];
+            u[2 * j] = cmulc(u[2 * j], make_float2(h.x, h.y));
+            u[2 * j + 1] = cmulc(u[2 * j + 1], make_float2(h.z, h.w));
+        }
+    }
+};
+
+template <int N, bool ESSFM>
+__global__ void __launch_bounds__(Geo<N>::T, 1) dbp_adj_kernel(const AdjParams q) {
+    using B = Blk<N>;
+    using G = Geo<N>;
+    const FwdParams &p = q.f;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    B blk(smem_raw, threadIdx.x);
+    float *red = reinterpret_cast<float *>(smem_raw + G::SMEM);
+    const int t = threadIdx.x;
+    const int blkid = blockIdx.x;
+    const int w = blkid / p.n_blocks;
+    const int b = blkid - w * p.n_blocks;
+    const long long n = p.n;
+    const int ns = p.n_steps;
+    const float2 *__restrict__ in = p.in + (size_t)w * 2 * n;
+    const float2 *__restrict__ gout = q.gout + (size_t)w * 2 * n;
+    const long long win0 = (long long)b * p.valid - p.half_overlap;
+    float4 *__restrict__ gb = q.gblk + (size_t)blkid * N;
+    float4 *__restrict__ ub = q.uscr + (size_t)blkid * N;
+    float4 *__restrict__ yb = q.yscr + (size_t)blkid * N;
+    float *__restrict__ part = q.part + (size_t)blkid * (ns * q.nr + ns);
+
+    blk.prefetch_h(p.H);
+    blk.load_tables(p.twA, p.twB, p.tw2);
+    typename B::Regs v;
+    blk.load_window(v, in, n, win0, p.boundary);
+
+    // output gradient in the block's valid region, zero in the discarded overlap
+    {
+        const int h = p.half_overlap;
+        const long long obase = (long long)b * p.valid - h;
+#pragma unroll
+        for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+            for (int j = 0; j < B::N2; ++j) {
+                const int e = blk.pos1(i, j);
+                const long long g = obase + e;
+                float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (e >= h && e < h + p.valid && g < n) {
+                    const float2 g0 = __ldg(gout + g), g1 = __ldg(gout + n + g);
+                    val = make_float4(g0.x, g0.y, g1.x, g1.y);
+                }
+                gb[e] = val;
+            }
+    }
+    __syncthreads();
+
+    MidMulH<N> mulh{blk.sH};
+    // ---- forward sweep: steps 0..ns-2, storing each next step's input
+    for (int s = 0; s + 1 < ns; ++s) {
+        if (s > 0) {
+            __syncthreads();
+            if (p.h_stride != 0) blk.prefetch_h(p.H + p.h_stride * s);
+        }
+        blk.pass1_fwd(v);
+        __syncthreads();
+        blk.template pass2<false>();
+        cp_async_wait_all();
+        __syncthreads();
+        blk.pass3(mulh);
+        __syncthreads();
+        blk.template pass2<true>();
+        __syncthreads();
+        blk.pass1_inv(v);
+        const float *__restrict__ a = p.taps + p.taps_stride * s;
+        if constexpr (ESSFM) {
+            __syncthreads();
+            blk.essfm_theta(v, a, p.n_tapblk);
+        }
+        const float a0 = __ldg(a);
+        float4 *ck = q.ckpt + ((size_t)blkid * (ns - 1) + s) * N;
+#pragma unroll
+        for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+            for (int j = 0; j < B::N2; ++j) {
+                const int e = blk.pos1(i, j);
+                const float th = ESSFM ? blk.farr(1)[pphys(e)] : a0 * joint_intensity(v[0][i][j], v[1][i][j]);
+                const float2 ex = expj(th);
+                v[0][i][j] = cmul(v[0][i][j], ex);
+                v[1][i][j] = cmul(v[1][i][j], ex);
+                ck[e] = make_float4(v[0][i][j].x, v[0][i][j].y, v[1][i][j].x, v[1][i][j].y);
+            }
+    }
+
+    // ---- reverse sweep
+    for (int s = ns - 1; s >= 0; --s) {
+        __syncthreads();
+        if (s < ns - 1) {
+            if (p.h_stride != 0) blk.prefetch_h(p.H + p.h_stride * s);
+            if (s == 0) {
+                blk.load_window(v, in, n, win0, p.boundary);
+            } else {
+                const float4 *ck = q.ckpt + ((size_t)blkid * (ns - 1) + (s - 1)) * N;
+#pragma unroll
+                for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+                    for (int j = 0; j < B::N2; ++j) {
+                        const float4 f = ck[blk.pos1(i, j)];
+                        v[0][i][j] = make_float2(f.x, f.y);
+                        v[1][i][j] = make_float2(f.z, f.w);
+                    }
+            }
+        } else if (ns > 1 && p.h_stride != 0) {
+            blk.prefetch_h(p.H + p.h_stride * s);
+        }
+        // recompute the linear sub-step, keeping U = H' X
+        MidRecompute<N> rec{blk.sH, ub};
+        blk.pass1_fwd(v);
+        __syncthreads();
+        blk.template pass2<false>();
+        cp_async_wait_all();
+        __syncthreads();
+        blk.pass3(rec);
+        __syncthreads();
+        blk.template pass2<true>();
+        __syncthreads();
+        blk.pass1_inv(v);   // v = y
+        const float *__restrict__ a = p.taps + p.taps_stride * s;
+        float *rp = part + s * q.nr;
+        if constexpr (ESSFM) {
+            __syncthreads();
+            blk.essfm_theta(v, a, p.n_tapblk);
+            float *sS = blk.farr(2);
+            const float *sT = blk.farr(1);
+#pragma unroll
+            for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+                for (int j = 0; j < B::N2; ++j) {
+                    const int e = blk.pos1(i, j);
+                    const float2 ex = expj(sT[pphys(e)]);
+                    const float2 y0 = v[0][i][j], y1 = v[1][i][j];
+                    const float2 z0 = cmul(y0, ex), z1 = cmul(y1, ex);
+                    const float4 g = gb[e];
+                    const float2 g0 = make_float2(g.x, g.y), g1 = make_float2(g.z, g.w);
+                    sS[pphys(e)] = MidAdjoint<N>::mimag(g0, z0) + MidAdjoint<N>::mimag(g1, z1);
+                    const float2 d0 = cmulc(g0, ex), d1 = cmulc(g1, ex);
+                    gb[e] = make_float4(d0.x, d0.y, d1.x, d1.y);
+                    yb[e] = make_float4(y0.x, y0.y, y1.x, y1.y);
+                }
+            __syncthreads();
+            // correlations R_i = sum_k s_k S_{k,i}, then dL/dP = filter(s) into farr(1)
+            {
+                const float *sP = blk.farr(0);
+                const int k0 = 16 * t;
+                float sk[16];
+                {
+                    const float4 *ps = reinterpret_cast<const float4 *>(sS + pphys(k0));
+                    const float4 *pp = reinterpret_cast<const float4 *>(sP + pphys(k0));
+                    float r0[1] = {0.f};
+#pragma unroll
+                    for (int qd = 0; qd < 4; ++qd) {
+                        const float4 fs = ps[qd], fp = pp[qd];
+                        sk[4 * qd + 0] = fs.x; sk[4 * qd + 1] = fs.y; sk[4 * qd + 2] = fs.z; sk[4 * qd + 3] = fs.w;
+                        r0[0] = fmaf(fs.x, fp.x, fmaf(fs.y, fp.y, fmaf(fs.z, fp.z, fmaf(fs.w, fp.w, r0[0]))));
+                    }
+                    block_sum<N, 1>(r0, red, rp, t);
+                }
+                for (int tb = 0; tb < p.n_tapblk; ++tb) {
+                    const int i0 = 8 * tb;
+                    float lw[24], rw[24];
+#pragma unroll
+                    for (int qd = 0; qd < 6; ++qd) {
+                        const int el = (k0 - i0 - 8 + 4 * qd) & (N - 1);
+                        const int er = (k0 + i0 + 4 * qd) & (N - 1);
+                        const float4 fl = *reinterpret_cast<const float4 *>(sP + pphys(el));
+                        const float4 fr = *reinterpret_cast<const float4 *>(sP + pphys(er));
+                        lw[4 * qd + 0] = fl.x; lw[4 * qd + 1] = fl.y; lw[4 * qd + 2] = fl.z; lw[4 * qd + 3] = fl.w;
+                        rw[4 * qd + 0] = fr.x; rw[4 * qd + 1] = fr.y; rw[4 * qd + 2] = fr.z; rw[4 * qd + 3] = fr.w;
+                    }
+                    float acc[8];
+#pragma unroll
+                    for (int ii = 1; ii <= 8; ++ii) {
+                        float x = 0.f;
+#pragma unroll
+                        for (int r = 0; r < 16; ++r) x = fmaf(sk[r], lw[r - ii + 8] + rw[r + ii], x);
+                        acc[ii - 1] = x;
+                    }
+                    block_sum<N, 8>(acc, red, rp + 1 + i0, t);
+                }
+                blk.fir16(sS, blk.farr(1), a, p.n_tapblk);
+            }
+            __syncthreads();
+            const float *sD = blk.farr(1);
+#pragma unroll
+            for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+                for (int j = 0; j < B::N2; ++j) {
+                    const int e = blk.pos1(i, j);
+                    const float dp2 = 2.f * sD[pphys(e)];
+                    const float4 g = gb[e], y = yb[e];
+                    v[0][i][j] = make_float2(fmaf(dp2, y.x, g.x), fmaf(dp2, y.y, g.y));
+                    v[1][i][j] = make_float2(fmaf(dp2, y.z, g.z), fmaf(dp2, y.w, g.w));
+                }
+        } else {
+            const float a0 = __ldg(a);
+            float r0[1] = {0.f};
+#pragma unroll
+            for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+                for (int j = 0; j < B::N2; ++j) {
+                    const int e = blk.pos1(i, j);
+                    const float2 y0 = v[0][i][j], y1 = v[1][i][j];
+                    const float pk = joint_intensity(y0, y1);
+                    const float2 ex = expj(a0 * pk);
+                    const float2 z0 = cmul(y0, ex), z1 = cmul(y1, ex);
+                    const float4 g = gb[e];
+                    const float2 g0 = make_float2(g.x, g.y), g1 = make_float2(g.z, g.w);
+                    const float sk = MidAdjoint<N>::mimag(g0, z0) + MidAdjoint<N>::mimag(g1, z1);
+                    r0[0] = fmaf(sk, pk, r0[0]);
+                    const float dp2 = 2.f * a0 * sk;
+                    const float2 d0 = cmulc(g0, ex), d1 = cmulc(g1, ex);
+                    v[0][i][j] = make_float2(fmaf(dp2, y0.x, d0.x), fmaf(dp2, y0.y, d0.y));
+                    v[1][i][j] = make_float2(fmaf(dp2, y1.x, d1.x), fmaf(dp2, y1.y, d1.y));
+                }
+            block_sum<N, 1>(r0, red, rp, t);
+        }
+        // linear adjoint: x conj(H'), with the step-length gradient
+        __syncthreads();
+        MidAdjoint<N> adj{blk.sH, ub, q.cphi, 0.f};
+        blk.pass1_fwd(v);
+        __syncthreads();
+        blk.template pass2<false>();
+        __syncthreads();
+        blk.pass3(adj);
+        __syncthreads();
+        blk.template pass2<true>();
+        __syncthreads();
+        blk.pass1_inv(v);   // v = g_x
+        {
+            float dz[1] = {adj.acc};
+            block_sum<N, 1>(dz, red, part + ns * q.nr + s, t);
+        }
+#pragma unroll
+        for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+            for (int j = 0; j < B::N2; ++j)
+                gb[blk.pos1(i, j)] = make_float4(v[0][i][j].x, v[0][i][j].y, v[1][i][j].x, v[1][i][j].y);
+    }
+}
+
+template <int N>
+int launch_adj_n(const AdjParams &q, int n_wave, bool essfm, cudaStream_t st) {
+    using G = Geo<N>;
+    static unsigned long long done_e = 0, done_s = 0;
+    const size_t smem = G::SMEM + (size_t)(G::T / 32) * 8 * sizeof(float);
+    const long long grid = (long long)q.f.n_blocks * n_wave;
+    if (grid <= 0 || grid > 0x7fffffffLL) return DBP_ERR_ARG;
+    if (essfm) {
+        if (!set_smem_once(dbp_adj_kernel<N, true>, smem, done_e)) return DBP_ERR_CUDA;
+        dbp_adj_kernel<N, true><<<(unsigned)grid, G::T, smem, st>>>(q);
+    } else {
+        if (!set_smem_once(dbp_adj_kernel<N, false>, smem, done_s)) return DBP_ERR_CUDA;
+        dbp_adj_kernel<N, false><<<(unsigned)grid, G::T, smem, st>>>(q);
+    }
+    return cudaGetLastError() == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
+}
+
+}  // namespace dbp

@@ -1,0 +1,377 @@
+// Building blocks of the fused DBP kernels: one CTA holds one overlap-save block of N
+// vector samples (both polarizations) and moves it through the steps of Section II.
+//
+// FFT (operations (i) and (iii) of Section II) in three passes, N = N2 * N1 * N0:
+//   pass 1  radix-N2 DFT over the top digit (stride N0 N1), twiddle W_N^{c k0}
+//   pass 2  radix-N1 DFT (stride N0), twiddle W_{N0 N1}^{n0 k1}
+//   pass 3  radix-N0 DFT (contiguous); the spectrum is then at digit-reversed positions
+// The inverse FFT runs the passes backwards with conjugate twiddles.  Pass 3 takes a
+// "mid" operation that works on the spectrum in registers between the forward and the
+// inverse radix-N0 DFTs (x H_s for the linear sub-step, Eq. 1; x conj(H_s) and the
+// step-length gradient for the adjoint).  Between passes the block lives in shared
+// memory, both polarizations as one float4 per position; before pass 1 and after pass
+// 1' it lives in registers in the pass-1 layout, where thread t owns positions
+// (t + T i) + S1 j.
+#pragma once
+#include "dbp_internal.cuh"
+#include "dft_regs.cuh"
+
+namespace dbp {
+
+template <int N0>
+__device__ __forceinline__ int xphys(int e) { return e + e / N0; }           // float4 slots
+template <int N0>
+__device__ __forceinline__ int hphys(int e) { return e + 2 * (e / N0); }     // float2 slots
+__device__ __forceinline__ int pphys(int e) { return e + 4 * (e >> 4); }     // float slots
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// exp(+j theta) for the nonlinear rotation.
+// Default: theta = q pi/2 + r with a three-constant Cody-Waite reduction (pi/2 =
+// 1.5703125 + 4.837512969970703e-4 + 7.549790126404332e-8; the first two constants have
+// 12 significant bits, so q times each is exact for |q| < 2^12, i.e. |theta| < 6400 rad),
+// then Taylor polynomials of sin and cos on |r| <= pi/4 (truncation below 2e-9, under
+// half an FP32 ulp), and the quadrant q mod 4 selects/negates.  With DBP_EXPJ_MUFU the
+// reduction is by 2 pi and the hardware sine/cosine approximations are used instead
+// (absolute error below 4e-7 on [-pi, pi]).
+__device__ __forceinline__ float2 expj(float th) {
+#ifdef DBP_EXPJ_MUFU
+    const float k = rintf(th * 0.15915494309189535f);
+    float r = fmaf(-k, 6.28125f, th);
+    r = fmaf(-k, 1.9353071795864769e-3f, r);
+    float s, c;
+    __sincosf(r, &s, &c);
+    return make_float2(c, s);
+#else
+    const float q = rintf(th * 0.63661977236758134f);
+    float r = fmaf(-q, 1.5703125f, th);
+    r = fmaf(-q, 4.837512969970703e-4f, r);
+    r = fmaf(-q, 7.549790126404332e-8f, r);
+    const float r2 = r * r;
+    // sin r = r - r^3/3! + r^5/5! - r^7/7! + r^9/9!
+    float ps = fmaf(r2, 2.7557319223985893e-6f, -1.9841269841269841e-4f);
+    ps = fmaf(r2, ps, 8.3333333333333333e-3f);
+    ps = fmaf(r2, ps, -1.6666666666666667e-1f);
+    const float sn = fmaf(r * r2, ps, r);
+    // cos r = 1 - r^2/2! + r^4/4! - r^6/6! + r^8/8! - r^10/10!
+    float pc = fmaf(r2, -2.7557319223985891e-7f, 2.4801587301587302e-5f);
+    pc = fmaf(r2, pc, -1.3888888888888889e-3f);
+    pc = fmaf(r2, pc, 4.1666666666666667e-2f);
+    pc = fmaf(r2, pc, -0.5f);
+    const float cs = fmaf(r2, pc, 1.0f);
+    const int quad = ((int)q) & 3;
+    const float c1 = (quad & 1) ? sn : cs;
+    const float s1 = (quad & 1) ? cs : sn;
+    return make_float2((quad == 1 || quad == 2) ? -c1 : c1, (quad >= 2) ? -s1 : s1);
+#endif
+}
+
+__device__ __forceinline__ float joint_intensity(float2 y0, float2 y1) {
+    return fmaf(y0.x, y0.x, fmaf(y0.y, y0.y, fmaf(y1.x, y1.x, y1.y * y1.y)));
+}
+
+template <int N>
+struct Blk {
+    using G = Geo<N>;
+    static constexpr int N0 = G::N0, N1 = G::N1, N2 = G::N2, T = G::T, S1 = G::S1;
+    static constexpr int C1 = 16 / N2;    // pass-1 columns per thread (both polarizations)
+    static constexpr int C2 = 16 / N1;    // pass-2 columns per thread (both polarizations)
+    using Regs = float2[2][C1][N2];
+
+    float4 *xs;
+    float2 *sH;
+    float2 *sA;
+    float2 *sB;
+    float2 *s2;
+    int t;
+
+    __device__ __forceinline__ Blk(unsigned char *smem, int tid)
+        : xs(reinterpret_cast<float4 *>(smem)),
+          sH(reinterpret_cast<float2 *>(smem + G::OFF_H)),
+          sA(reinterpret_cast<float2 *>(smem + G::OFF_TWA)),
+          sB(reinterpret_cast<float2 *>(smem + G::OFF_TWB)),
+          s2(reinterpret_cast<float2 *>(smem + G::OFF_TW2)),
+          t(tid) {}
+
+    // float views of the block buffer for the nonlinear sub-step (valid while the block
+    // is in registers): k = 0 joint intensity, 1 phase, 2 (adjoint) phase gradient.
+    __device__ __forceinline__ float *farr(int k) const { return reinterpret_cast<float *>(xs) + k * G::PADP; }
+
+    __device__ __forceinline__ int pos1(int i, int j) const { return (t + T * i) + S1 * j; }
+
+    // Twiddle tables (k-major: twA [N2][16], twB [N2][N0 N1/16], tw2 [N1][N0]).
+    __device__ __forceinline__ void load_tables(const float2 *twA, const float2 *twB, const float2 *tw2) {
+        for (int i = t; i < G::TWA; i += T) sA[i] = __ldg(twA + i);
+        for (int i = t; i < G::TWB; i += T) sB[i] = __ldg(twB + i);
+        for (int i = t; i < G::TW2; i += T) s2[i] = __ldg(tw2 + i);
+    }
+
+    // Copies one step's H table (N float2, 16-byte chunks) into padded shared memory.
+    __device__ __forceinline__ void prefetch_h(const float2 *__restrict__ H) {
+#pragma unroll
+        for (int q = 0; q < (N / 2) / T; ++q) {
+            const int e = 2 * (t + T * q);
+            cp_async16(sH + hphys<N0>(e), H + e);
+        }
+        cp_async_commit();
+    }
+
+    // Block window [win0, win0 + N) of both polarizations of a waveform (pol-major
+    // [2][n] complex64) into the pass-1 layout; periodic or zero outside [0, n).
+    __device__ __forceinline__ void load_window(Regs &v, const float2 *__restrict__ in, long long n, long long win0,
+                                                int boundary) const {
+        if (win0 >= 0 && win0 + N <= n) {
+#pragma unroll
+            for (int pol = 0; pol < 2; ++pol)
+#pragma unroll
+                for (int i = 0; i < C1; ++i)
+#pragma unroll
+                    for (int j = 0; j < N2; ++j) v[pol][i][j] = __ldg(in + pol * n + win0 + pos1(i, j));
+        } else {
+#pragma unroll
+            for (int pol = 0; pol < 2; ++pol)
+#pragma unroll
+                for (int i = 0; i < C1; ++i)
+#pragma unroll
+                    for (int j = 0; j < N2; ++j) {
+                        long long idx = win0 + pos1(i, j);
+                        float2 val = make_float2(0.f, 0.f);
+                        if (boundary == DBP_PERIODIC) {
+                            idx %= n;
+                            if (idx < 0) idx += n;
+                            val = __ldg(in + pol * n + idx);
+                        } else if (idx >= 0 && idx < n) {
+                            val = __ldg(in + pol * n + idx);
+                        }
+                        v[pol][i][j] = val;
+                    }
+        }
+    }
+
+    // pass 1 (forward): DFT over the top digit, twiddle, registers -> shared memory
+    __device__ __forceinline__ void pass1_fwd(Regs &v) {
+#pragma unroll
+        for (int i = 0; i < C1; ++i) {
+            const int c = t + T * i;
+            const float2 *ta = sA + (c & 15);
+            const float2 *tb = sB + (c >> 4);
+            Dft<N2, false>::run(v[0][i]);
+            Dft<N2, false>::run(v[1][i]);
+#pragma unroll
+            for (int k = 1; k < N2; ++k) {
+                const float2 wk = cmul(ta[16 * k], tb[(S1 / 16) * k]);
+                v[0][i][k] = cmul(v[0][i][k], wk);
+                v[1][i][k] = cmul(v[1][i][k], wk);
+            }
+#pragma unroll
+            for (int k = 0; k < N2; ++k)
+                xs[xphys<N0>(c + S1 * k)] = make_float4(v[0][i][k].x, v[0][i][k].y, v[1][i][k].x, v[1][i][k].y);
+        }
+    }
+
+    // pass 2: radix N1, stride N0 (forward: DFT then twiddle; inverse: conj twiddle then IDFT)
+    template <bool INV>
+    __device__ __forceinline__ void pass2() {
+#pragma unroll
+        for (int i = 0; i < C2; ++i) {
+            const int c2 = t + T * i;
+            const int n0 = c2 % N0, k0 = c2 / N0;
+            const int base = n0 + S1 * k0;
+            float2 u0[N1], u1[N1];
+#pragma unroll
+            for (int j = 0; j < N1; ++j) {
+                const float4 f = xs[xphys<N0>(base + N0 * j)];
+                u0[j] = make_float2(f.x, f.y);
+                u1[j] = make_float2(f.z, f.w);
+            }
+            const float2 *tw = s2 + n0;
+            if constexpr (!INV) {
+                Dft<N1, false>::run(u0);
+                Dft<N1, false>::run(u1);
+#pragma unroll
+                for (int k = 1; k < N1; ++k) {
+                    const float2 wk = tw[N0 * k];
+                    u0[k] = cmul(u0[k], wk);
+                    u1[k] = cmul(u1[k], wk);
+                }
+            } else {
+#pragma unroll
+                for (int k = 1; k < N1; ++k) {
+                    const float2 wk = tw[N0 * k];
+                    u0[k] = cmulc(u0[k], wk);
+                    u1[k] = cmulc(u1[k], wk);
+                }
+                Dft<N1, true>::run(u0);
+                Dft<N1, true>::run(u1);
+            }
+#pragma unroll
+            for (int k = 0; k < N1; ++k)
+                xs[xphys<N0>(base + N0 * k)] = make_float4(u0[k].x, u0[k].y, u1[k].x, u1[k].y);
+        }
+    }
+
+    // pass 3: contiguous radix-N0 DFT, mid operation on the spectrum, inverse DFT.
+    // N0 == 16: thread t owns positions 16t..16t+15 of both polarizations and calls
+    //           mid(u0, u1, base);  N0 == 32: thread t owns polarization t & 1 of
+    //           positions 32(t>>1).. and calls mid.one(u, pol, base).
+    template <class Mid>
+    __device__ __forceinline__ void pass3(Mid &mid) {
+        if constexpr (N0 == 16) {
+            const int base = 16 * t;
+            float2 u0[16], u1[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float4 f = xs[xphys<16>(base + j)];
+                u0[j] = make_float2(f.x, f.y);
+                u1[j] = make_float2(f.z, f.w);
+            }
+            Dft<16, false>::run(u0);
+            Dft<16, false>::run(u1);
+            mid.two(u0, u1, base);
+            Dft<16, true>::run(u0);
+            Dft<16, true>::run(u1);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) xs[xphys<16>(base + j)] = make_float4(u0[j].x, u0[j].y, u1[j].x, u1[j].y);
+        } else {
+            const int pol = t & 1;
+            const int base = N0 * (t >> 1);
+            float2 *xh = reinterpret_cast<float2 *>(xs);
+            float2 u[N0];
+#pragma unroll
+            for (int j = 0; j < N0; ++j) u[j] = xh[2 * xphys<N0>(base + j) + pol];
+            Dft<N0, false>::run(u);
+            mid.one(u, pol, base);
+            Dft<N0, true>::run(u);
+#pragma unroll
+            for (int j = 0; j < N0; ++j) xh[2 * xphys<N0>(base + j) + pol] = u[j];
+        }
+    }
+
+    // pass 1' (inverse): conjugate twiddle, inverse radix-N2 DFT, shared memory -> registers
+    __device__ __forceinline__ void pass1_inv(Regs &v) const {
+#pragma unroll
+        for (int i = 0; i < C1; ++i) {
+            const int c = t + T * i;
+            const float2 *ta = sA + (c & 15);
+            const float2 *tb = sB + (c >> 4);
+#pragma unroll
+            for (int j = 0; j < N2; ++j) {
+                const float4 f = xs[xphys<N0>(c + S1 * j)];
+                v[0][i][j] = make_float2(f.x, f.y);
+                v[1][i][j] = make_float2(f.z, f.w);
+            }
+#pragma unroll
+            for (int k = 1; k < N2; ++k) {
+                const float2 wk = cmul(ta[16 * k], tb[(S1 / 16) * k]);
+                v[0][i][k] = cmulc(v[0][i][k], wk);
+                v[1][i][k] = cmulc(v[1][i][k], wk);
+            }
+            Dft<N2, true>::run(v[0][i]);
+            Dft<N2, true>::run(v[1][i]);
+        }
+    }
+
+    // Symmetric filter over 16 consecutive positions 16t..16t+15 (circular in the block):
+    // out_k = a_0 src_k + sum_{i=1}^{8 n_tapblk} a_i (src_{k-i} + src_{k+i}), read from
+    // the float array src and written to dst (both pphys-indexed).  Eq. 3 when src = P.
+    __device__ __forceinline__ void fir16(const float *src, float *dst, const float *__restrict__ a,
+                                          int n_tapblk) const {
+        const int k0 = 16 * t;
+        float th[16];
+        {
+            const float4 *pc = reinterpret_cast<const float4 *>(src + pphys(k0));
+            const float a0 = __ldg(a);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 f = pc[q];
+                th[4 * q + 0] = a0 * f.x;
+                th[4 * q + 1] = a0 * f.y;
+                th[4 * q + 2] = a0 * f.z;
+                th[4 * q + 3] = a0 * f.w;
+            }
+        }
+        for (int blk = 0; blk < n_tapblk; ++blk) {
+            const int i0 = 8 * blk;
+            float lw[24], rw[24];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const int el = (k0 - i0 - 8 + 4 * q) & (N - 1);
+                const int er = (k0 + i0 + 4 * q) & (N - 1);
+                const float4 fl = *reinterpret_cast<const float4 *>(src + pphys(el));
+                const float4 fr = *reinterpret_cast<const float4 *>(src + pphys(er));
+                lw[4 * q + 0] = fl.x; lw[4 * q + 1] = fl.y; lw[4 * q + 2] = fl.z; lw[4 * q + 3] = fl.w;
+                rw[4 * q + 0] = fr.x; rw[4 * q + 1] = fr.y; rw[4 * q + 2] = fr.z; rw[4 * q + 3] = fr.w;
+            }
+#pragma unroll
+            for (int ii = 1; ii <= 8; ++ii) {
+                const float ai = __ldg(a + i0 + ii);
+#pragma unroll
+                for (int r = 0; r < 16; ++r) th[r] = fmaf(ai, lw[r - ii + 8] + rw[r + ii], th[r]);
+            }
+        }
+        float4 *pt = reinterpret_cast<float4 *>(dst + pphys(k0));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pt[q] = make_float4(th[4 * q], th[4 * q + 1], th[4 * q + 2], th[4 * q + 3]);
+    }
+
+    // ESSFM phase theta (Eq. 3) of the block in registers, into farr(1).  The block
+    // buffer must be free (a barrier after the last pass-1' read); returns after a
+    // barrier, with theta visible to all threads.
+    __device__ __forceinline__ void essfm_theta(const Regs &v, const float *__restrict__ a, int n_tapblk) {
+        float *sP = farr(0);
+#pragma unroll
+        for (int i = 0; i < C1; ++i)
+#pragma unroll
+            for (int j = 0; j < N2; ++j) sP[pphys(pos1(i, j))] = joint_intensity(v[0][i][j], v[1][i][j]);
+        __syncthreads();
+        fir16(sP, farr(1), a, n_tapblk);
+        __syncthreads();
+    }
+};
+
+// Multiplies the spectrum by the step's H table in shared memory (Eq. 1, inverted).
+template <int N>
+struct MidMulH {
+    const float2 *sH;
+    __device__ __forceinline__ void two(float2 (&u0)[16], float2 (&u1)[16], int base) {
+        const float4 *hrow = reinterpret_cast<const float4 *>(sH + hphys<16>(base));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 h = hrow[j];
+            u0[2 * j] = cmul(u0[2 * j], make_float2(h.x, h.y));
+            u1[2 * j] = cmul(u1[2 * j], make_float2(h.x, h.y));
+            u0[2 * j + 1] = cmul(u0[2 * j + 1], make_float2(h.z, h.w));
+            u1[2 * j + 1] = cmul(u1[2 * j + 1], make_float2(h.z, h.w));
+        }
+    }
+    template <int R>
+    __device__ __forceinline__ void one(float2 (&u)[R], int, int base) {
+        const float4 *hrow = reinterpret_cast<const float4 *>(sH + hphys<R>(base));
+#pragma unroll
+        for (int j = 0; j < R / 2; ++j) {
+            const float4 h = hrow[j];
+            u[2 * j] = cmul(u[2 * j], make_float2(h.x, h.y));
+            u[2 * j + 1] = cmul(u[2 * j + 1], make_float2(h.z, h.w));
+        }
+    }
+};
+
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per device.
+template <typename K>
+inline bool set_smem_once(K kernel, size_t bytes, unsigned long long &done_mask) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    const unsigned long long bit = 1ull << dev;
+    if (done_mask & bit) return true;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return false;
+    done_mask |= bit;
+    return true;
+}
+
+}  // namespace dbp

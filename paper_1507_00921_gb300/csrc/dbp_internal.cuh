@@ -85,6 +85,12 @@ struct PlanImpl {
     // host copies
     double *step_dz = nullptr;
     double *step_geff = nullptr;
+    float *coeffs = nullptr;        // [n_steps][n_taps + 1] unscaled c_{s,i}
+    // adjoint: device copies of c and gamma_eff, and scratch (allocated on first dbp_grad)
+    float *d_craw = nullptr;
+    double *d_geff = nullptr;
+    void *d_adj = nullptr;
+    size_t adj_bytes = 0;
     // host-staging scratch for dbp_run_host
     void *d_stage_in = nullptr;
     void *d_stage_out = nullptr;
@@ -101,6 +107,17 @@ int launch(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_
 __global__ void build_h_kernel(float2 *H, int N, int n0, int n1, int n2, double beta2, double fs, const double *dz,
                                int n_tables);
 __global__ void build_twiddle_kernel(float2 *twA, float2 *twB, float2 *tw2, int N, int n0, int n1, int n2);
+
+struct AdjParams;
+int launch_adj_512(const AdjParams &, int n_wave, bool essfm, cudaStream_t);
+int launch_adj_1024(const AdjParams &, int n_wave, bool essfm, cudaStream_t);
+int launch_adj_2048(const AdjParams &, int n_wave, bool essfm, cudaStream_t);
+int launch_adj_4096(const AdjParams &, int n_wave, bool essfm, cudaStream_t);
+int launch_adj_8192(const AdjParams &, int n_wave, bool essfm, cudaStream_t);
+int upload_taps(PlanImpl &P, const float *host_coeffs);
+int dev_alloc(void **p, size_t bytes);
+int build_h_tables(PlanImpl &P);
+void fill_fwd_params(const PlanImpl &P, FwdParams &p);
 
 // Kernel launchers (one translation unit per block length).
 int launch_fwd_512(const FwdParams &, int n_wave, bool essfm, cudaStream_t);

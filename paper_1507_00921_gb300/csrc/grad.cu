@@ -1,0 +1,201 @@
+// dbp_grad and dbp_set_steps: the reverse-mode gradient of the fused DBP and the update
+// of the step table it is usually paired with (fitting step lengths / nonlinear
+// strengths by gradient descent).
+//
+// dbp_grad launches, on the caller's stream:
+//   1. dbp_adj_kernel: one CTA per overlap-save block; block input gradients and
+//      per-block partial sums of R_{s,i} = sum_k s_k S_{k,i} and dL/ddz_s to scratch;
+//   2. gather_kernel: overlap-add of the block input gradients (Section III's
+//      overlap-and-save transposed), each input sample summing its covering blocks in
+//      block order;
+//   3. reduce_kernel: FP64 sums of the partials over blocks in a fixed order;
+//   4. finalize_kernel: dL/dc_{s,i} = gamma_eff_s R_{s,i} (summed over steps when the
+//      coefficients are shared), dL/dgamma_eff_s = sum_i c_{s,i} R_{s,i}, dL/ddz_s.
+// No floating-point atomics: results are bitwise reproducible.
+#include <math.h>
+#include <stdlib.h>
+
+#include "adj_kernel.cuh"
+
+namespace dbp {
+
+__global__ void gather_kernel(const float4 *__restrict__ gblk, float2 *__restrict__ gin, long long n, int nb, int V,
+                              int half, int N, int boundary, int n_wave) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n_wave) return;
+    const long long w = idx / n, j = idx - w * n;
+    const float4 *gw = gblk + (size_t)w * nb * N;
+    float sx = 0.f, sy = 0.f, sz = 0.f, sw = 0.f;
+    if (n >= N) {
+        const int m0 = boundary == DBP_PERIODIC ? -1 : 0, m1 = boundary == DBP_PERIODIC ? 1 : 0;
+        for (int m = m0; m <= m1; ++m) {
+            const long long jp = j + m * n;                 // position in unwrapped block coordinates
+            long long blo = jp + half - N + 1;              // st_b <= jp < st_b + N, st_b = b V - half
+            blo = blo <= 0 ? 0 : (blo + V - 1) / V;
+            long long bhi = jp + half < 0 ? -1 : (jp + half) / V;
+            if (bhi > nb - 1) bhi = nb - 1;
+            for (long long b = blo; b <= bhi; ++b) {
+                const long long e = jp - (b * V - half);
+                if (e < 0 || e >= N) continue;
+                const float4 g = gw[(size_t)b * N + e];
+                sx += g.x; sy += g.y; sz += g.z; sw += g.w;
+            }
+        }
+    } else {
+        for (int b = 0; b < nb; ++b) {
+            const long long st = (long long)b * V - half;
+            if (boundary == DBP_PERIODIC) {
+                long long e = (j - st) % n;
+                if (e < 0) e += n;
+                for (; e < N; e += n) {
+                    const float4 g = gw[(size_t)b * N + e];
+                    sx += g.x; sy += g.y; sz += g.z; sw += g.w;
+                }
+            } else {
+                const long long e = j - st;
+                if (e >= 0 && e < N) {
+                    const float4 g = gw[(size_t)b * N + e];
+                    sx += g.x; sy += g.y; sz += g.z; sw += g.w;
+                }
+            }
+        }
+    }
+    float2 *gp = gin + (size_t)w * 2 * n;
+    gp[j] = make_float2(sx, sy);
+    gp[n + j] = make_float2(sz, sw);
+}
+
+// out[q] = sum over blocks b (fixed order) of part[b * stride + q], in FP64.
+__global__ void reduce_kernel(const float *__restrict__ part, long long blocks, int stride, double *out) {
+    __shared__ double sm[256];
+    const int q = blockIdx.x;
+    double acc = 0.0;
+    for (long long b = threadIdx.x; b < blocks; b += blockDim.x) acc += (double)part[(size_t)b * stride + q];
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = sm[0];
+}
+
+__global__ void finalize_kernel(const double *sums, const float *craw, const double *geff, int ns, int nt, int nr,
+                                int per_step, float *d_coeffs, float *d_gamma, float *d_dz) {
+    const int t = threadIdx.x;
+    const double *R = sums, *DZ = sums + (size_t)ns * nr;
+    for (int q = t; q < ns * (nt + 1); q += blockDim.x) {
+        const int s = q / (nt + 1), i = q % (nt + 1);
+        if (d_coeffs && per_step) d_coeffs[q] = (float)(geff[s] * R[s * nr + i]);
+    }
+    if (d_coeffs && !per_step)
+        for (int i = t; i <= nt; i += blockDim.x) {
+            double acc = 0.0;
+            for (int s = 0; s < ns; ++s) acc += geff[s] * R[s * nr + i];
+            d_coeffs[i] = (float)acc;
+        }
+    for (int s = t; s < ns; s += blockDim.x) {
+        if (d_gamma) {
+            double acc = 0.0;
+            for (int i = 0; i <= nt; ++i) acc += (double)craw[s * (nt + 1) + i] * R[s * nr + i];
+            d_gamma[s] = (float)acc;
+        }
+        if (d_dz) d_dz[s] = (float)DZ[s];
+    }
+}
+
+static int launch_adj(const PlanImpl &P, const AdjParams &q, int n_wave, cudaStream_t st) {
+    const bool essfm = P.method == DBP_ESSFM;
+    switch (P.info.fft_size) {
+        case 512: return launch_adj_512(q, n_wave, essfm, st);
+        case 1024: return launch_adj_1024(q, n_wave, essfm, st);
+        case 2048: return launch_adj_2048(q, n_wave, essfm, st);
+        case 4096: return launch_adj_4096(q, n_wave, essfm, st);
+        case 8192: return launch_adj_8192(q, n_wave, essfm, st);
+        default: return DBP_ERR_INFEASIBLE;
+    }
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace dbp
+
+using namespace dbp;
+
+extern "C" int dbp_grad(dbp_plan_t *plan, const void *in, const void *grad_out, void *grad_in, float *d_coeffs,
+                        float *d_gamma_eff, float *d_step_len, dbp_stream_t stream) {
+    if (!plan || !in || !grad_out) return DBP_ERR_ARG;
+    PlanImpl &P = plan->impl;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = P.info.fft_size, ns = P.info.n_steps, nt = P.info.n_taps;
+    const int nw = P.signal.n_waveforms;
+    const long long blocks = (long long)P.info.n_blocks * nw;
+    const int nr = 1 + 8 * P.n_tapblk;
+    const int stride = ns * nr + ns;
+    const size_t wbytes = (size_t)2 * P.signal.n_samples * sizeof(float2) * nw;
+    if (grad_in && (overlaps(grad_in, in, wbytes) || overlaps(grad_in, grad_out, wbytes))) return DBP_ERR_ALIAS;
+
+    // scratch: gblk, uscr, yscr, checkpoints, partials, sums
+    const size_t fld = (size_t)blocks * N * sizeof(float4);
+    const size_t o_g = 0, o_u = al256(fld), o_y = o_u + al256(fld);
+    const size_t o_c = o_y + al256(fld);
+    const size_t o_p = o_c + al256(fld * (ns > 1 ? ns - 1 : 1));
+    const size_t o_s = o_p + al256(sizeof(float) * (size_t)blocks * stride);
+    const size_t total = o_s + al256(sizeof(double) * stride);
+    if (P.adj_bytes < total) {
+        if (P.d_adj) cudaFree(P.d_adj);
+        P.d_adj = nullptr;
+        P.adj_bytes = 0;
+        if (dev_alloc(&P.d_adj, total)) return DBP_ERR_ALLOC;
+        P.adj_bytes = total;
+    }
+    unsigned char *sc = (unsigned char *)P.d_adj;
+    AdjParams q;
+    fill_fwd_params(P, q.f);
+    q.f.in = (const float2 *)in;
+    q.f.out = nullptr;
+    q.gout = (const float2 *)grad_out;
+    q.gblk = (float4 *)(sc + o_g);
+    q.uscr = (float4 *)(sc + o_u);
+    q.yscr = (float4 *)(sc + o_y);
+    q.ckpt = (float4 *)(sc + o_c);
+    q.part = (float *)(sc + o_p);
+    q.nr = nr;
+    const double fsn = P.signal.sample_rate_hz / N;
+    q.cphi = (float)(2.0 * M_PI * M_PI * P.info.beta2_s2_per_m * fsn * fsn);
+    int rc = launch_adj(P, q, nw, st);
+    if (rc) return rc;
+    if (grad_in) {
+        const long long total_s = P.signal.n_samples * nw;
+        gather_kernel<<<(unsigned)((total_s + 255) / 256), 256, 0, st>>>(
+            q.gblk, (float2 *)grad_in, P.signal.n_samples, P.info.n_blocks, P.info.valid, P.info.overlap / 2, N,
+            P.signal.boundary, nw);
+    }
+    double *sums = (double *)(sc + o_s);
+    reduce_kernel<<<stride, 256, 0, st>>>(q.part, blocks, stride, sums);
+    finalize_kernel<<<1, 256, 0, st>>>(sums, P.d_craw, P.d_geff, ns, nt, nr, P.coeffs_per_step, d_coeffs, d_gamma_eff,
+                                       d_step_len);
+    return cudaGetLastError() == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
+}
+
+extern "C" int dbp_set_steps(dbp_plan_t *plan, const double *step_len_m, const double *gamma_eff) {
+    if (!plan) return DBP_ERR_ARG;
+    PlanImpl &P = plan->impl;
+    const int ns = P.info.n_steps;
+    if (step_len_m)
+        for (int s = 0; s < ns; ++s)
+            if (!(step_len_m[s] >= 0) || !isfinite(step_len_m[s])) return DBP_ERR_ARG;
+    if (gamma_eff)
+        for (int s = 0; s < ns; ++s)
+            if (!isfinite(gamma_eff[s])) return DBP_ERR_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return DBP_ERR_CUDA;
+    if (step_len_m) {
+        for (int s = 0; s < ns; ++s) P.step_dz[s] = step_len_m[s];
+        const int rc = build_h_tables(P);
+        if (rc) return rc;
+    }
+    if (gamma_eff) {
+        for (int s = 0; s < ns; ++s) P.step_geff[s] = gamma_eff[s];
+    }
+    return upload_taps(P, P.coeffs);
+}

@@ -167,19 +167,23 @@ int describe(const dbp_link *link, const dbp_signal *sig, const dbp_steps *st, d
     return DBP_OK;
 }
 
-static int upload_taps(PlanImpl &P, const float *host_coeffs) {
+int upload_taps(PlanImpl &P, const float *host_coeffs) {
     const int ns = P.info.n_steps, nt = P.info.n_taps;
     float *h = (float *)calloc((size_t)ns * P.taps_stride, sizeof(float));
     if (!h) return DBP_ERR_ALLOC;
     for (int s = 0; s < ns; ++s) {
         const float *c = host_coeffs ? host_coeffs + (P.coeffs_per_step ? (size_t)s * (nt + 1) : 0) : nullptr;
         for (int i = 0; i <= nt; ++i) {
-            const double ci = c ? (double)c[i] : (i == 0 ? 1.0 : 0.0);
-            h[(size_t)s * P.taps_stride + i] = (float)(P.step_geff[s] * ci);
+            const float ci = c ? c[i] : (i == 0 ? 1.0f : 0.0f);
+            P.coeffs[(size_t)s * (nt + 1) + i] = ci;
+            h[(size_t)s * P.taps_stride + i] = (float)(P.step_geff[s] * (double)ci);
         }
     }
     cudaError_t e = cudaMemcpy(P.d_taps, h, (size_t)ns * P.taps_stride * sizeof(float), cudaMemcpyHostToDevice);
     free(h);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P.d_craw, P.coeffs, sizeof(float) * (size_t)ns * (nt + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P.d_geff, P.step_geff, sizeof(double) * ns, cudaMemcpyHostToDevice);
     return e == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
 }
 
@@ -195,8 +199,12 @@ static void release(PlanImpl &P) {
         if (s) cudaStreamDestroy(s);
     for (auto &e : P.ev)
         if (e) cudaEventDestroy(e);
+    if (P.d_craw) cudaFree(P.d_craw);
+    if (P.d_geff) cudaFree(P.d_geff);
+    if (P.d_adj) cudaFree(P.d_adj);
     free(P.step_dz);
     free(P.step_geff);
+    free(P.coeffs);
 }
 
 static bool fault_inject_alloc() {
@@ -204,9 +212,40 @@ static bool fault_inject_alloc() {
     return f && strcmp(f, "alloc") == 0;
 }
 
-static int dev_alloc(void **p, size_t bytes) {
+int dev_alloc(void **p, size_t bytes) {
     if (fault_inject_alloc()) return DBP_ERR_ALLOC;
     return cudaMalloc(p, bytes) == cudaSuccess ? DBP_OK : DBP_ERR_ALLOC;
+}
+
+// (Re)builds the H_s tables from P.step_dz on the GPU in FP64, synchronously; one table
+// when all steps have the same length.
+int build_h_tables(PlanImpl &P) {
+    const int ns = P.info.n_steps, N = P.info.fft_size;
+    bool shared = true;
+    for (int s = 1; s < ns; ++s)
+        if (P.step_dz[s] != P.step_dz[0]) shared = false;
+    const int n_tables = shared ? 1 : ns;
+    const int had = P.d_H ? (P.h_shared ? 1 : ns) : 0;
+    if (had < n_tables) {
+        if (P.d_H) cudaFree(P.d_H);
+        P.d_H = nullptr;
+        if (dev_alloc((void **)&P.d_H, sizeof(float2) * (size_t)N * n_tables)) return DBP_ERR_ALLOC;
+    }
+    P.h_shared = shared;
+    int n0, n1, n2;
+    host_geo(N, n0, n1, n2);
+    double *d_dz = nullptr;
+    int rc = dev_alloc((void **)&d_dz, sizeof(double) * n_tables);
+    if (!rc && cudaMemcpy(d_dz, P.step_dz, sizeof(double) * n_tables, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = DBP_ERR_CUDA;
+    if (!rc) {
+        dim3 g((N + 255) / 256, n_tables);
+        build_h_kernel<<<g, 256>>>(P.d_H, N, n0, n1, n2, P.info.beta2_s2_per_m, P.signal.sample_rate_hz, d_dz,
+                                   n_tables);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) rc = DBP_ERR_CUDA;
+    }
+    if (d_dz) cudaFree(d_dz);
+    return rc;
 }
 
 static int make_plan(const dbp_link *link, const dbp_signal *sig, const dbp_steps *st, dbp_plan_t **out) {
@@ -228,16 +267,13 @@ static int make_plan(const dbp_link *link, const dbp_signal *sig, const dbp_step
     const int ns = st->n_steps, N = st->fft_size;
     P.step_dz = (double *)malloc(sizeof(double) * ns);
     P.step_geff = (double *)malloc(sizeof(double) * ns);
-    if (!P.step_dz || !P.step_geff) {
+    P.coeffs = (float *)malloc(sizeof(float) * (size_t)ns * (st->n_taps + 1));
+    if (!P.step_dz || !P.step_geff || !P.coeffs) {
         release(P);
         delete plan;
         return DBP_ERR_ALLOC;
     }
     describe(link, sig, st, nullptr, P.step_dz, P.step_geff);
-    P.h_shared = true;
-    for (int s = 1; s < ns; ++s)
-        if (P.step_dz[s] != P.step_dz[0]) P.h_shared = false;
-    const int n_tables = P.h_shared ? 1 : ns;
     if (cudaGetDevice(&P.device) != cudaSuccess) {
         release(P);
         delete plan;
@@ -245,22 +281,17 @@ static int make_plan(const dbp_link *link, const dbp_signal *sig, const dbp_step
     }
     int n0, n1, n2;
     host_geo(N, n0, n1, n2);
-    double *d_dz = nullptr;
-    rc = dev_alloc((void **)&P.d_H, sizeof(float2) * (size_t)N * n_tables);
+    rc = build_h_tables(P);
     if (!rc) rc = dev_alloc((void **)&P.d_taps, sizeof(float) * (size_t)ns * P.taps_stride);
+    if (!rc) rc = dev_alloc((void **)&P.d_craw, sizeof(float) * (size_t)ns * (st->n_taps + 1));
+    if (!rc) rc = dev_alloc((void **)&P.d_geff, sizeof(double) * ns);
     if (!rc) rc = dev_alloc((void **)&P.d_twA, sizeof(float2) * (size_t)16 * n2);
     if (!rc) rc = dev_alloc((void **)&P.d_twB, sizeof(float2) * (size_t)(n0 * n1 / 16) * n2);
     if (!rc) rc = dev_alloc((void **)&P.d_tw2, sizeof(float2) * (size_t)n0 * n1);
-    if (!rc) rc = dev_alloc((void **)&d_dz, sizeof(double) * n_tables);
-    if (!rc && cudaMemcpy(d_dz, P.step_dz, sizeof(double) * n_tables, cudaMemcpyHostToDevice) != cudaSuccess)
-        rc = DBP_ERR_CUDA;
     if (!rc) {
-        dim3 g((N + 255) / 256, n_tables);
-        build_h_kernel<<<g, 256>>>(P.d_H, N, n0, n1, n2, info.beta2_s2_per_m, sig->sample_rate_hz, d_dz, n_tables);
         build_twiddle_kernel<<<(N + 255) / 256, 256>>>(P.d_twA, P.d_twB, P.d_tw2, N, n0, n1, n2);
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) rc = DBP_ERR_CUDA;
     }
-    if (d_dz) cudaFree(d_dz);
     if (!rc) rc = upload_taps(P, st->coeffs);
     if (rc) {
         release(P);
@@ -276,10 +307,9 @@ bool overlaps(const void *a, const void *b, size_t bytes) {
     return x < y + bytes && y < x + bytes;
 }
 
-int launch(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_t st) {
-    FwdParams p;
-    p.in = (const float2 *)in;
-    p.out = (float2 *)out;
+void fill_fwd_params(const PlanImpl &P, FwdParams &p) {
+    p.in = nullptr;
+    p.out = nullptr;
     p.n = P.signal.n_samples;
     p.n_blocks = P.info.n_blocks;
     p.valid = P.info.valid;
@@ -294,6 +324,13 @@ int launch(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_
     p.twA = P.d_twA;
     p.twB = P.d_twB;
     p.tw2 = P.d_tw2;
+}
+
+int launch(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_t st) {
+    FwdParams p;
+    fill_fwd_params(P, p);
+    p.in = (const float2 *)in;
+    p.out = (float2 *)out;
     const bool essfm = P.method == DBP_ESSFM;
     switch (P.info.fft_size) {
         case 512: return launch_fwd_512(p, n_wave, essfm, st);

@@ -147,6 +147,41 @@ class Plan:
         _lib.check(rc, "dbp_run_host")
         return out
 
+    def grad(self, x, g_out, need_input=True, stream=None):
+        """Reverse-mode gradient of ``run`` at input x for g_out = dL/dRe(out) + j dL/dIm(out).
+
+        Returns ``(g_in, d_coeffs, d_gamma_eff, d_step_len)``: g_in (complex64, like x, or
+        None), d_coeffs (float32 [n_steps, n_taps+1] if coeffs_per_step else [n_taps+1]),
+        d_gamma_eff and d_step_len (float32 [n_steps]), all on the plan's device."""
+        import torch
+        self._check_tensor(x, "x")
+        self._check_tensor(g_out, "g_out")
+        ns, nt = self.info.n_steps, self.info.n_taps
+        g_in = torch.empty_like(x) if need_input else None
+        shape_c = (ns, nt + 1) if self.coeffs_per_step else (nt + 1,)
+        d_c = torch.empty(shape_c, dtype=torch.float32, device=self.device)
+        d_g = torch.empty(ns, dtype=torch.float32, device=self.device)
+        d_z = torch.empty(ns, dtype=torch.float32, device=self.device)
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        rc = self._lib.dbp_grad(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(g_out.data_ptr()),
+                                C.c_void_p(g_in.data_ptr() if g_in is not None else 0), C.c_void_p(d_c.data_ptr()),
+                                C.c_void_p(d_g.data_ptr()), C.c_void_p(d_z.data_ptr()), C.c_void_p(st.cuda_stream))
+        _lib.check(rc, "dbp_grad")
+        return g_in, d_c, d_g, d_z
+
+    def set_steps(self, step_len_m=None, gamma_eff=None):
+        """Replace the step lengths (rebuilds H_s) and/or nonlinear strengths gamma_eff_s."""
+        dp = C.POINTER(C.c_double)
+        dz = None if step_len_m is None else np.ascontiguousarray(step_len_m, dtype=np.float64)
+        ge = None if gamma_eff is None else np.ascontiguousarray(gamma_eff, dtype=np.float64)
+        rc = self._lib.dbp_set_steps(self._h, dz.ctypes.data_as(dp) if dz is not None else dp(),
+                                     ge.ctypes.data_as(dp) if ge is not None else dp())
+        _lib.check(rc, "dbp_set_steps")
+        if dz is not None:
+            self.info.step_dz = dz.copy()
+        if ge is not None:
+            self.info.step_gamma_eff = ge.copy()
+
     def set_coeffs(self, coeffs):
         c = np.ascontiguousarray(coeffs, dtype=np.float32)
         rc = self._lib.dbp_set_coeffs(self._h, c.ctypes.data_as(C.POINTER(C.c_float)))
@@ -168,3 +203,54 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _autograd():
+    import torch
+
+    class DBPFunction(torch.autograd.Function):
+        """out = DBP(x; c) through libdbp; backward through dbp_grad (gradients with
+        respect to the waveform and the ESSFM coefficients)."""
+
+        @staticmethod
+        def forward(ctx, x, coeffs, plan):
+            c = coeffs.detach().to("cpu", torch.float32).numpy()
+            plan.set_coeffs(c)
+            ctx.plan = plan
+            ctx.coeffs = c
+            ctx.c_device, ctx.c_dtype = coeffs.device, coeffs.dtype
+            ctx.save_for_backward(x)
+            return plan.run(x.contiguous())
+
+        @staticmethod
+        def backward(ctx, g_out):
+            (x,) = ctx.saved_tensors
+            plan = ctx.plan
+            plan.set_coeffs(ctx.coeffs)
+            g_in, d_c, _, _ = plan.grad(x, g_out.contiguous(), need_input=ctx.needs_input_grad[0])
+            return g_in, d_c.reshape(ctx.coeffs.shape).to(ctx.c_device, ctx.c_dtype), None
+
+    class DBP(torch.nn.Module):
+        """ESSFM/SSFM backpropagation with trainable coefficients (a torch module over a Plan)."""
+
+        def __init__(self, plan, coeffs=None):
+            super().__init__()
+            nt = plan.info.n_taps
+            shape = (plan.info.n_steps, nt + 1) if plan.coeffs_per_step else (nt + 1,)
+            if coeffs is None:
+                coeffs = np.zeros(shape, dtype=np.float32)
+                coeffs[..., 0] = 1.0
+            self.plan = plan
+            self.coeffs = torch.nn.Parameter(torch.as_tensor(np.asarray(coeffs, dtype=np.float32)).reshape(shape))
+
+        def forward(self, x):
+            return DBPFunction.apply(x, self.coeffs, self.plan)
+
+    return DBPFunction, DBP
+
+
+def __getattr__(name):
+    if name in ("DBPFunction", "DBP"):
+        f, m = _autograd()
+        return f if name == "DBPFunction" else m
+    raise AttributeError(name)

@@ -94,6 +94,8 @@ def test_null_arguments_and_strerror():
     assert lib.dbp_plan_get_info(None, None) == _lib.DBP_ERR_ARG
     assert lib.dbp_set_coeffs(None, None) == _lib.DBP_ERR_ARG
     assert lib.dbp_plan(None, None, None, None) == _lib.DBP_ERR_ARG
+    assert lib.dbp_grad(None, None, None, None, None, None, None, None) == _lib.DBP_ERR_ARG
+    assert lib.dbp_set_steps(None, None, None) == _lib.DBP_ERR_ARG
     lib.dbp_destroy(None)
     for code in range(-7, 1):
         assert lib.dbp_strerror(code) not in (b"", b"unknown error")
