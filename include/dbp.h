@@ -203,6 +203,36 @@ int dbp_run_host(dbp_plan_t *plan, const void *in, void *out, dbp_stream_t strea
 int dbp_run_noalloc(const dbp_link *link, const dbp_signal *signal, const dbp_steps *steps,
                     const void *in, void *out, dbp_stream_t stream);
 
+/*
+ * Batched launch of many jobs of uneven size (plans of any block length, link length,
+ * step count and filter length, each with its own DEVICE in/out buffers).  A batch is
+ * built once and replayed: jobs are grouped by block length, each group is served by a
+ * persistent kernel whose CTAs pop (job, waveform, block) items from a device counter,
+ * and the group kernels are captured as parallel branches of one CUDA graph.  Plans and
+ * buffers must stay alive and unchanged in place while the batch exists.
+ * flags: 0, or DBP_BATCH_STREAMING: every job's input is read only after
+ * dbp_batch_publish(job) (a producer may fill inputs while the batch runs).  A job that
+ * is not published within timeout_us microseconds (0 = 1 s) is skipped and the batch
+ * reports DBP_ERR_TIMEOUT; the wait never hangs.
+ */
+#define DBP_BATCH_STREAMING 1
+typedef struct dbp_batch dbp_batch_t;
+int dbp_batch_create(dbp_plan_t *const *plans, const void *const *ins, void *const *outs, int n_jobs, int flags,
+                     int timeout_us, dbp_batch_t **out);
+/* Resets the work counters (and, when streaming, clears the publish flags) on `stream`,
+ * then launches the batch graph after them.  Asynchronous. */
+int dbp_batch_run(dbp_batch_t *batch, dbp_stream_t stream);
+/* Streaming batches: marks job `job` (index into the create-time lists) as ready, on
+ * `stream`, ordered after the flag reset of the latest dbp_batch_run.  Uses a copy, not
+ * a kernel, so it proceeds while the batch occupies the SMs. */
+int dbp_batch_publish(dbp_batch_t *batch, int job, dbp_stream_t stream);
+/* Waits for the device and returns the batch status: DBP_OK or DBP_ERR_TIMEOUT. */
+int dbp_batch_status(dbp_batch_t *batch);
+void dbp_batch_destroy(dbp_batch_t *batch);
+/* One-shot: create, run on `stream`, wait, destroy.  Returns the batch status. */
+int dbp_run_batch(dbp_plan_t *const *plans, const void *const *ins, void *const *outs, int n_jobs,
+                  dbp_stream_t stream);
+
 /* Frees the plan's device tables and scratch (synchronizes the device first). */
 void dbp_destroy(dbp_plan_t *plan);
 

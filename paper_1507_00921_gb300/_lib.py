@@ -28,6 +28,7 @@ DBP_PERIODIC, DBP_ZERO = 0, 1
 DBP_SSFM, DBP_ESSFM = 0, 1
 DBP_FP32 = 0
 DBP_MAX_TAPS = 64
+DBP_BATCH_STREAMING = 1
 DBP_MAX_STEPS = 1024
 
 
@@ -75,6 +76,13 @@ _PROTOS = {
     "dbp_set_steps": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "dbp_run_noalloc": (C.c_int, [C.POINTER(dbp_link), C.POINTER(dbp_signal), C.POINTER(dbp_steps), _P, _P, _P]),
     "dbp_destroy": (None, [_P]),
+    "dbp_batch_create": (C.c_int, [C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.c_int, C.c_int, C.c_int,
+                                   C.POINTER(_P)]),
+    "dbp_batch_run": (C.c_int, [_P, _P]),
+    "dbp_batch_publish": (C.c_int, [_P, C.c_int, _P]),
+    "dbp_batch_status": (C.c_int, [_P]),
+    "dbp_batch_destroy": (None, [_P]),
+    "dbp_run_batch": (C.c_int, [C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.c_int, _P]),
     "dbp_strerror": (C.c_char_p, [C.c_int]),
     "dbp_version": (C.c_char_p, []),
     "dbp_diag_fma": (C.c_int, [_P, C.c_int, C.c_int, _P]),

@@ -66,6 +66,15 @@ struct FwdParams {
     const float2 *tw2;      // [N1][N0] W_{N0 N1}^{n0 k1}
 };
 
+// One job of a batched launch: a plan's parameters with its own input/output buffers.
+struct BatchJob {
+    FwdParams p;
+    long long item0;        // first item of this job within its block-length group
+    int essfm;
+    int pad;
+    const int *ready;       // publish flag (non-zero: input is in place)
+};
+
 struct PlanImpl {
     dbp_link link;
     dbp_signal signal;
@@ -118,6 +127,17 @@ int upload_taps(PlanImpl &P, const float *host_coeffs);
 int dev_alloc(void **p, size_t bytes);
 int build_h_tables(PlanImpl &P);
 void fill_fwd_params(const PlanImpl &P, FwdParams &p);
+
+int prepare_batch_512(long long n_items, int *grid);
+int launch_batch_512(const BatchJob *, int, long long, unsigned long long *, int *, int, int, cudaStream_t);
+int prepare_batch_1024(long long n_items, int *grid);
+int launch_batch_1024(const BatchJob *, int, long long, unsigned long long *, int *, int, int, cudaStream_t);
+int prepare_batch_2048(long long n_items, int *grid);
+int launch_batch_2048(const BatchJob *, int, long long, unsigned long long *, int *, int, int, cudaStream_t);
+int prepare_batch_4096(long long n_items, int *grid);
+int launch_batch_4096(const BatchJob *, int, long long, unsigned long long *, int *, int, int, cudaStream_t);
+int prepare_batch_8192(long long n_items, int *grid);
+int launch_batch_8192(const BatchJob *, int, long long, unsigned long long *, int *, int, int, cudaStream_t);
 
 // Kernel launchers (one translation unit per block length).
 int launch_fwd_512(const FwdParams &, int n_wave, bool essfm, cudaStream_t);

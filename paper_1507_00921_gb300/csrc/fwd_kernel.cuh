@@ -16,24 +16,18 @@
 
 namespace dbp {
 
+// One overlap-save block (waveform w, block b) of the plan described by p, with the
+// twiddle tables already in shared memory and p.H (step 0) prefetch committed.
 template <int N, bool ESSFM>
-__global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const FwdParams p) {
+__device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, int w, int b) {
     using B = Blk<N>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    B blk(smem_raw, threadIdx.x);
-
-    const int w = blockIdx.x / p.n_blocks;
-    const int b = blockIdx.x - w * p.n_blocks;
     const long long n = p.n;
     const float2 *__restrict__ in = p.in + (size_t)w * 2 * n;
     float2 *__restrict__ out = p.out + (size_t)w * 2 * n;
     const long long win0 = (long long)b * p.valid - p.half_overlap;
 
-    blk.prefetch_h(p.H);
-    blk.load_tables(p.twA, p.twB, p.tw2);
     typename B::Regs v;
     blk.load_window(v, in, n, win0, p.boundary);
-    __syncthreads();   // twiddle tables visible
 
     MidMulH<N> mid{blk.sH};
     for (int s = 0; s < p.n_steps; ++s) {
@@ -94,6 +88,18 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
         }
 }
 
+template <int N, bool ESSFM>
+__global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const FwdParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Blk<N> blk(smem_raw, threadIdx.x);
+    const int w = blockIdx.x / p.n_blocks;
+    const int b = blockIdx.x - w * p.n_blocks;
+    blk.prefetch_h(p.H);
+    blk.load_tables(p.twA, p.twB, p.tw2);
+    __syncthreads();   // twiddle tables visible
+    process_block<N, ESSFM>(p, blk, w, b);
+}
+
 template <int N>
 int launch_fwd_n(const FwdParams &p, int n_wave, bool essfm, cudaStream_t st) {
     using G = Geo<N>;
@@ -107,6 +113,96 @@ int launch_fwd_n(const FwdParams &p, int n_wave, bool essfm, cudaStream_t st) {
         if (!set_smem_once(dbp_fwd_kernel<N, false>, G::SMEM, done_ssfm)) return DBP_ERR_CUDA;
         dbp_fwd_kernel<N, false><<<(unsigned)grid, G::T, G::SMEM, st>>>(p);
     }
+    return cudaGetLastError() == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
+}
+
+}  // namespace dbp
+
+namespace dbp {
+
+// Persistent batched DBP over many jobs (plans) of block length N: each CTA pops
+// (job, waveform, block) items from a device counter until the size group is done.
+// Every job has a publish flag; a CTA waits for it with a bounded spin (nanosleep
+// between polls, at most max_spins polls) and, if it never appears, records
+// DBP_ERR_TIMEOUT in *error and skips the item.  Once an error is recorded, waiting
+// CTAs give up immediately.
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB)
+    dbp_batch_kernel(const BatchJob *__restrict__ jobs, int n_jobs, long long n_items,
+                     unsigned long long *counter, int *error, int max_spins) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ FwdParams sp;
+    __shared__ long long s_item;
+    __shared__ int s_job, s_ok, s_essfm, s_w, s_b;
+    Blk<N> blk(smem_raw, threadIdx.x);
+    const int t = threadIdx.x;
+    blk.load_tables(jobs[0].p.twA, jobs[0].p.twB, jobs[0].p.tw2);
+    for (;;) {
+        if (t == 0) s_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= n_items) break;
+        if (t == 0) {
+            int lo = 0, hi = n_jobs - 1;                 // last job with item0 <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (jobs[mid].item0 <= item) lo = mid; else hi = mid - 1;
+            }
+            const BatchJob &J = jobs[lo];
+            int ok = 1;
+            const volatile int *flag = J.ready;
+            for (int spins = 0; *flag == 0;) {
+                if (*(volatile int *)error != 0 || ++spins > max_spins) {
+                    atomicCAS(error, 0, DBP_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(1000);
+            }
+            __threadfence();
+            s_ok = ok;
+            s_job = lo;
+            s_essfm = J.essfm;
+            sp = J.p;
+            const long long local = item - J.item0;
+            s_w = (int)(local / J.p.n_blocks);
+            s_b = (int)(local - (long long)s_w * J.p.n_blocks);
+        }
+        __syncthreads();
+        if (s_ok) {
+            blk.prefetch_h(sp.H);
+            if (s_essfm)
+                process_block<N, true>(sp, blk, s_w, s_b);
+            else
+                process_block<N, false>(sp, blk, s_w, s_b);
+        }
+        __syncthreads();   // shared memory free for the next item
+    }
+}
+
+// Grid of the persistent batch kernel (one wave of resident CTAs, at most n_items);
+// also opts the kernel into its shared memory.  Call before any stream capture.
+template <int N>
+int prepare_batch_n(long long n_items, int *grid) {
+    using G = Geo<N>;
+    static unsigned long long done = 0;
+    if (!set_smem_once(dbp_batch_kernel<N>, G::SMEM, done)) return DBP_ERR_CUDA;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dbp_batch_kernel<N>, G::T, G::SMEM) != cudaSuccess)
+        return DBP_ERR_CUDA;
+    long long g = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (g > n_items) g = n_items;
+    *grid = (int)(g < 1 ? 1 : g);
+    return DBP_OK;
+}
+
+template <int N>
+int launch_batch_n(const BatchJob *jobs, int n_jobs, long long n_items, unsigned long long *counter, int *error,
+                   int max_spins, int grid, cudaStream_t st) {
+    using G = Geo<N>;
+    dbp_batch_kernel<N><<<(unsigned)grid, G::T, G::SMEM, st>>>(jobs, n_jobs, n_items, counter, error, max_spins);
     return cudaGetLastError() == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
 }
 

@@ -205,6 +205,61 @@ class Plan:
         self.close()
 
 
+class Batch:
+    """Many plans with their own device buffers, backpropagated by one CUDA-graph launch
+    of persistent kernels (libdbp's dbp_batch_*).  Buffers must stay alive and in place."""
+
+    def __init__(self, plans, ins, outs, streaming=False, timeout_us=0):
+        self._lib = _lib.load()
+        n = len(plans)
+        if not (n == len(ins) == len(outs)) or n == 0:
+            raise ValueError("plans, ins and outs must be non-empty lists of equal length")
+        for pl, x, y in zip(plans, ins, outs):
+            pl._check_tensor(x, "in")
+            pl._check_tensor(y, "out")
+        self._keep = (list(plans), list(ins), list(outs))
+        arr = C.c_void_p * n
+        self._p = arr(*[pl._h.value for pl in plans])
+        self._i = arr(*[x.data_ptr() for x in ins])
+        self._o = arr(*[y.data_ptr() for y in outs])
+        h = C.c_void_p()
+        rc = self._lib.dbp_batch_create(self._p, self._i, self._o, n,
+                                        _lib.DBP_BATCH_STREAMING if streaming else 0, int(timeout_us), C.byref(h))
+        _lib.check(rc, "dbp_batch_create")
+        self._h = h
+
+    def run(self, stream=None):
+        import torch
+        st = torch.cuda.current_stream() if stream is None else stream
+        _lib.check(self._lib.dbp_batch_run(self._h, C.c_void_p(st.cuda_stream)), "dbp_batch_run")
+
+    def publish(self, job, stream=None):
+        import torch
+        st = torch.cuda.current_stream() if stream is None else stream
+        _lib.check(self._lib.dbp_batch_publish(self._h, int(job), C.c_void_p(st.cuda_stream)), "dbp_batch_publish")
+
+    def status(self):
+        """Waits for the device; returns 0 or a negative DBP_ERR_* code (e.g. timeout)."""
+        return self._lib.dbp_batch_status(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.dbp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def _autograd():
     import torch
 

@@ -136,3 +136,23 @@ def received_like(n_waveforms: int, n_symbols: int, launch_dbm: float, seed: int
     for b in range(n_waveforms):
         out[b] = cache[b % len(cache)]
     return out
+
+
+def batch_jobs(n_jobs: int, seed: int, min_log2_symbols: int = 12, max_log2_symbols: int = 18):
+    """Seeded uneven job list for batched backpropagation: symbol counts log-uniform in
+    [2^min, 2^max], links of 10/20/30/40 spans (800-3200 km), launch powers uniform in
+    0-4 dBm, and a mix of multi-step SSFM (5-20 steps) and 1-2 step ESSFM (8-32 taps)."""
+    g = rng(seed)
+    jobs = []
+    for j in range(n_jobs):
+        log2s = g.uniform(min_log2_symbols, max_log2_symbols)
+        n_sym = int(round(2.0 ** log2s))
+        spans = int(g.choice([10, 20, 30, 40]))
+        dbm = float(g.uniform(0.0, 4.0))
+        if g.random() < 0.5:
+            method, ns, nc = "ssfm", int(g.integers(5, 21)), 0
+        else:
+            method, ns, nc = "essfm", int(g.integers(1, 3)), int(g.choice([8, 16, 24, 32]))
+        jobs.append(dict(n_symbols=n_sym, n_spans=spans, launch_dbm=dbm, method=method, n_steps=ns, n_taps=nc,
+                         seed=seed + 10 * j))
+    return jobs

@@ -96,6 +96,11 @@ def test_null_arguments_and_strerror():
     assert lib.dbp_plan(None, None, None, None) == _lib.DBP_ERR_ARG
     assert lib.dbp_grad(None, None, None, None, None, None, None, None) == _lib.DBP_ERR_ARG
     assert lib.dbp_set_steps(None, None, None) == _lib.DBP_ERR_ARG
+    assert lib.dbp_batch_create(None, None, None, 0, 0, 0, None) == _lib.DBP_ERR_ARG
+    assert lib.dbp_batch_run(None, None) == _lib.DBP_ERR_ARG
+    assert lib.dbp_batch_publish(None, 0, None) == _lib.DBP_ERR_ARG
+    assert lib.dbp_batch_status(None) == _lib.DBP_ERR_ARG
+    lib.dbp_batch_destroy(None)
     lib.dbp_destroy(None)
     for code in range(-7, 1):
         assert lib.dbp_strerror(code) not in (b"", b"unknown error")

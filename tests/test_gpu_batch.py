@@ -1,0 +1,122 @@
+"""Batched uneven workloads through one CUDA-graph launch of persistent kernels: each
+job's output equals its own dbp_run; replays are identical; streaming jobs wait for
+their publish flag with a bounded spin and a never-published job ends in
+DBP_ERR_TIMEOUT without hanging."""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+FS = synth.SAMPLE_RATE
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def fft_for(spans, method, ns, nc):
+    """Smallest supported block length at least twice the overlap."""
+    from paper_1507_00921_gb300 import describe
+    for n in (1024, 2048, 4096, 8192):
+        try:
+            info = describe(synth.link(spans), FS, 4096, method=method, n_steps=ns, n_taps=nc, fft_size=n)
+        except Exception:
+            continue
+        if n >= 2 * info.overlap:
+            return n
+    return 8192
+
+
+def make_jobs(torch, n_jobs, seed, max_log2=13):
+    from paper_1507_00921_gb300 import Plan
+    plans, ins, outs = [], [], []
+    for k, jb in enumerate(synth.batch_jobs(n_jobs, seed, 9, max_log2)):
+        n = jb["n_symbols"] * synth.SPS
+        nc = jb["n_taps"]
+        coeffs = None
+        if nc:
+            c = 0.6 * np.exp(-np.arange(nc + 1) / 8.0)
+            coeffs = (c / (c[0] + 2 * c[1:].sum())).astype(np.float32)
+        nw = 1 + (k % 3)
+        fft = fft_for(jb["n_spans"], jb["method"], jb["n_steps"], nc)
+        plans.append(Plan(synth.link(jb["n_spans"]), FS, n, n_waveforms=nw, method=jb["method"],
+                          n_steps=jb["n_steps"], n_taps=nc, coeffs=coeffs, fft_size=fft,
+                          boundary="zero" if k % 4 == 3 else "periodic"))
+        x = synth.random_field(nw, n, synth.dbm_to_w(jb["launch_dbm"]), seed=jb["seed"]).astype(np.complex64)
+        ins.append(torch.from_numpy(x).cuda())
+        outs.append(torch.zeros_like(ins[-1]))
+    return plans, ins, outs
+
+
+def test_batch_equals_individual_runs_and_replays(torch_cuda):
+    torch = torch_cuda
+    from paper_1507_00921_gb300 import Batch
+    plans, ins, outs = make_jobs(torch, 14, 501)
+    assert len({p.info.fft_size for p in plans}) >= 2
+    refs = [p.run(x) for p, x in zip(plans, ins)]
+    with Batch(plans, ins, outs) as batch:
+        batch.run()
+        assert batch.status() == 0
+        first = [o.clone() for o in outs]
+        for o in outs:
+            o.zero_()
+        batch.run()
+        assert batch.status() == 0
+    for o, f, r in zip(outs, first, refs):
+        assert torch.equal(o, f)
+        err = (o - r).abs().max().item() / r.abs().max().item()
+        assert err <= 1e-6, err
+    for p in plans:
+        p.close()
+
+
+def test_streaming_publish_and_bounded_timeout(torch_cuda):
+    torch = torch_cuda
+    from paper_1507_00921_gb300 import Batch, _lib
+    plans, ins, outs = make_jobs(torch, 4, 777, max_log2=11)
+    refs = [p.run(x) for p, x in zip(plans, ins)]
+    side = torch.cuda.Stream()
+    with Batch(plans, ins, outs, streaming=True, timeout_us=20000) as batch:
+        batch.run()
+        for j in range(4):
+            batch.publish(j, stream=side)
+        assert batch.status() == 0
+        for o, r in zip(outs, refs):
+            assert (o - r).abs().max().item() <= 1e-6 * r.abs().max().item()
+        for o in outs:
+            o.zero_()
+        t0 = time.time()
+        batch.run()
+        for j in (0, 1, 3):                       # job 2 is never published
+            batch.publish(j, stream=side)
+        assert batch.status() == _lib.DBP_ERR_TIMEOUT
+        assert time.time() - t0 < 30.0
+        for j in (0, 1, 3):
+            assert (outs[j] - refs[j]).abs().max().item() <= 1e-6 * refs[j].abs().max().item()
+        assert outs[2].abs().max().item() == 0.0
+    for p in plans:
+        p.close()
+
+
+def test_run_batch_one_shot(torch_cuda):
+    torch = torch_cuda
+    import ctypes as C
+    from paper_1507_00921_gb300 import _lib
+    plans, ins, outs = make_jobs(torch, 3, 99, max_log2=11)
+    lib = _lib.load()
+    arr = C.c_void_p * 3
+    rc = lib.dbp_run_batch(arr(*[p._h.value for p in plans]), arr(*[x.data_ptr() for x in ins]),
+                           arr(*[y.data_ptr() for y in outs]), 3, None)
+    assert rc == 0
+    for p, x, y in zip(plans, ins, outs):
+        r = p.run(x)
+        torch.cuda.synchronize()
+        assert (y - r).abs().max().item() <= 1e-6 * r.abs().max().item()
+        p.close()
