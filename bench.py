@@ -230,6 +230,10 @@ def run_ours(args):
         dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
     e2e_value = world * vs * k_e2e / t_e2e.item() / 1e6
 
+    batch = None
+    if args.batch_jobs > 0:
+        batch = batch_measure(torch, args.batch_jobs, 5, stream)
+    fp32 = fp32_pipe(value / world, fft_e, pe.info.overlap)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds, fft_e)
@@ -253,6 +257,8 @@ def run_ours(args):
                          "bytes_per_vector_sample": BYTES_PER_VSAMPLE},
             "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(x_host.nbytes),
                     "d2h_bytes_per_step": int(x_host.nbytes), "steps": k_e2e},
+            "fp32_pipe": fp32,
+            "batch": batch,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -262,6 +268,87 @@ def run_ours(args):
     ps.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def batch_measure(torch, n_jobs: int, reps: int, stream):
+    """Uneven workload: n_jobs waveforms (log-uniform 2^12..2^18 symbols, 800-3200 km,
+    0-4 dBm, SSFM 5-20 steps / ESSFM 1-2 steps with 8-32 taps), block length autotuned
+    per link length and method; one graph launch of the batch vs the same jobs launched
+    one by one.  Returns aggregate vector samples/s of both."""
+    from paper_1507_00921_gb300 import Batch, Plan, autotune
+    jobs = synth.batch_jobs(n_jobs, synth.BASE_SEED + 5)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.BASE_SEED + 5)
+    tuned = {}
+    plans, ins, outs = [], [], []
+    total = 0
+    for jb in jobs:
+        link = synth.link(jb["n_spans"])
+        key = (jb["n_spans"], jb["method"])
+        if key not in tuned:
+            rep = (1, ESSFM_TAPS) if jb["method"] == "essfm" else (20, 0)
+            tuned[key] = autotune.tune(link, synth.SAMPLE_RATE, jb["method"], rep[0], rep[1])
+        n = jb["n_symbols"] * synth.SPS
+        nc = jb["n_taps"]
+        coeffs = essfm_coeffs(nc) if nc else None
+        plan = None
+        for fft in sorted({tuned[key], 2048, 4096, 8192}):
+            if fft < tuned[key]:
+                continue
+            try:
+                plan = Plan(link, synth.SAMPLE_RATE, n, method=jb["method"], n_steps=jb["n_steps"], n_taps=nc,
+                            coeffs=coeffs, fft_size=fft)
+                break
+            except Exception:
+                continue
+        x = torch.randn((1, 2, n), dtype=torch.complex64, device="cuda", generator=gen)
+        x *= math.sqrt(synth.dbm_to_w(jb["launch_dbm"]))
+        plans.append(plan)
+        ins.append(x)
+        outs.append(torch.empty_like(x))
+        total += n
+    batch = Batch(plans, ins, outs)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            fn()
+            fn()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    t_batch = timed(lambda: batch.run(stream))
+    status = batch.status()
+
+    def sequential():
+        for p, x, y in zip(plans, ins, outs):
+            p.run(x, y, stream=stream)
+    t_seq = timed(sequential)
+    batch.close()
+    for p in plans:
+        p.close()
+    return {"value": round(total / t_batch / 1e6, 1), "unit": UNIT, "jobs": n_jobs, "vector_samples": total,
+            "one_by_one": round(total / t_seq / 1e6, 1), "speedup": round(t_seq / t_batch, 3), "status": status,
+            "block_lengths": {f"{k[0] * 80}km_{k[1]}": v for k, v in sorted(tuned.items())},
+            "launches": "1 CUDA graph launch (persistent kernel per block length)"}
+
+
+def fp32_pipe(value_msps: float, fft: int, overlap: int):
+    """Section III operation count of one ESSFM step per output vector sample (radix-2
+    FFT count), at the measured rate, against the FP32 FMA peak measured now."""
+    from paper_1507_00921_gb300 import complexity, peaks
+    flops = complexity.mults_per_sample(fft, overlap, ESSFM_TAPS) + complexity.adds_per_sample(fft, overlap,
+                                                                                                 ESSFM_TAPS)
+    achieved = flops * value_msps * 1e6 / 1e12
+    peak = peaks.fp32_fma_peak_tflops()["fp32_tflops"]
+    return {"paper_flops_per_vector_sample": round(flops, 1), "achieved_tflops": round(achieved, 2),
+            "peak_tflops": round(peak, 1), "peak_kind": "measured (FMA microbenchmark, this run)",
+            "frac": round(achieved / peak, 4)}
 
 
 # ---------------------------------------------------------------------- CPU oracle
@@ -334,6 +421,7 @@ def main():
     ap.add_argument("--fft-size", type=int, default=0, help="0 = autotune over {2048, 4096, 8192}")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-jobs", type=int, default=256, help="uneven batched workload size (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
