@@ -153,6 +153,20 @@ struct Blk {
         }
     }
 
+    // Prefetches a block window's 2 x N complex64 samples into L2 (128-byte lines),
+    // clamped to [0, n); a hint only, for the block that will run on this SM next.
+    __device__ __forceinline__ void prefetch_window_l2(const float2 *in, long long n, long long win0) const {
+        const long long lo = win0 < 0 ? 0 : win0;
+        const long long hi = win0 + N > n ? n : win0 + N;
+        if (hi <= lo) return;
+        const char *base0 = reinterpret_cast<const char *>(in + lo);
+        const long long bytes = (hi - lo) * (long long)sizeof(float2);
+        for (long long off = (long long)t * 128; off < bytes; off += (long long)T * 128) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(base0 + off));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(base0 + off + n * (long long)sizeof(float2)));
+        }
+    }
+
     // pass 1 (forward): DFT over the top digit, twiddle, registers -> shared memory
     __device__ __forceinline__ void pass1_fwd(Regs &v) {
 #pragma unroll

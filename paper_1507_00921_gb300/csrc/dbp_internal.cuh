@@ -64,6 +64,7 @@ struct FwdParams {
     const float2 *twA;      // [N2][16] W_N^{cl k}
     const float2 *twB;      // [N2][N0 N1 / 16] W_{N/16}^{ch k}
     const float2 *tw2;      // [N1][N0] W_{N0 N1}^{n0 k1}
+    int prefetch_ahead;     // blocks ahead whose input window is prefetched into L2 (0: off)
 };
 
 // One job of a batched launch: a plan's parameters with its own input/output buffers.
@@ -84,6 +85,7 @@ struct PlanImpl {
     int n_tapblk;
     int taps_stride;
     bool h_shared;            // all steps share one H table
+    int prefetch_ahead = -1;  // L2 prefetch distance in blocks (-1: one wave of resident CTAs)
     int device;
     // device tables
     float2 *d_H = nullptr;

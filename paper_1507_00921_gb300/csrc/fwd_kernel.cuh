@@ -96,8 +96,25 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
     const int b = blockIdx.x - w * p.n_blocks;
     blk.prefetch_h(p.H);
     blk.load_tables(p.twA, p.twB, p.tw2);
+    if (p.prefetch_ahead > 0 && blockIdx.x + p.prefetch_ahead < gridDim.x) {
+        const unsigned nb = blockIdx.x + p.prefetch_ahead;
+        const int w2 = nb / p.n_blocks, b2 = nb - w2 * p.n_blocks;
+        blk.prefetch_window_l2(p.in + (size_t)w2 * 2 * p.n, p.n, (long long)b2 * p.valid - p.half_overlap);
+    }
     __syncthreads();   // twiddle tables visible
     process_block<N, ESSFM>(p, blk, w, b);
+}
+
+// SMs x resident CTAs per SM for a kernel configuration (at least 1).
+template <typename K>
+inline int resident_ctas(K kernel, int threads, size_t smem) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess)
+        return 1;
+    const int r = sms * per_sm;
+    return r > 0 ? r : 1;
 }
 
 template <int N>
@@ -106,12 +123,20 @@ int launch_fwd_n(const FwdParams &p, int n_wave, bool essfm, cudaStream_t st) {
     static unsigned long long done_essfm = 0, done_ssfm = 0;
     const long long grid = (long long)p.n_blocks * n_wave;
     if (grid <= 0 || grid > 0x7fffffffLL) return DBP_ERR_ARG;
+    static int resident[64][2];   // CTAs resident per GPU (SMs x CTAs per SM), per device and variant
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DBP_ERR_CUDA;
+    FwdParams q = p;
     if (essfm) {
         if (!set_smem_once(dbp_fwd_kernel<N, true>, G::SMEM, done_essfm)) return DBP_ERR_CUDA;
-        dbp_fwd_kernel<N, true><<<(unsigned)grid, G::T, G::SMEM, st>>>(p);
+        if (!resident[dev][1]) resident[dev][1] = resident_ctas(dbp_fwd_kernel<N, true>, G::T, G::SMEM);
+        if (q.prefetch_ahead < 0) q.prefetch_ahead = resident[dev][1];
+        dbp_fwd_kernel<N, true><<<(unsigned)grid, G::T, G::SMEM, st>>>(q);
     } else {
         if (!set_smem_once(dbp_fwd_kernel<N, false>, G::SMEM, done_ssfm)) return DBP_ERR_CUDA;
-        dbp_fwd_kernel<N, false><<<(unsigned)grid, G::T, G::SMEM, st>>>(p);
+        if (!resident[dev][0]) resident[dev][0] = resident_ctas(dbp_fwd_kernel<N, false>, G::T, G::SMEM);
+        if (q.prefetch_ahead < 0) q.prefetch_ahead = resident[dev][0];
+        dbp_fwd_kernel<N, false><<<(unsigned)grid, G::T, G::SMEM, st>>>(q);
     }
     return cudaGetLastError() == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
 }

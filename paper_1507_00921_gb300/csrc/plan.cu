@@ -324,6 +324,7 @@ void fill_fwd_params(const PlanImpl &P, FwdParams &p) {
     p.twA = P.d_twA;
     p.twB = P.d_twB;
     p.tw2 = P.d_tw2;
+    p.prefetch_ahead = P.prefetch_ahead;
 }
 
 int launch(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_t st) {
