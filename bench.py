@@ -170,6 +170,8 @@ def autotune(torch, method, n_wave, x, y, stream, candidates=(2048, 4096, 8192))
 def run_ours(args):
     import torch
     import torch.distributed as dist
+
+    from paper_1507_00921_gb300 import dist as pdist
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -203,14 +205,11 @@ def run_ours(args):
     k_s = max(3, args.steps // 20)
     t_s = time_device(torch, ps, x, y, k_s, max(3, args.warmup // 4), stream)
     barrier()
-    times = torch.tensor([t_e, t_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    t_e, t_s = times.tolist()
+    t_e, t_s = pdist.max_over_ranks([t_e, t_s], device="cuda")
 
     vs = B * N_SAMPLES                    # vector samples per rank per step
-    value = world * vs * args.steps / t_e / 1e6
-    ssfm_value = world * vs * k_s / t_s / 1e6
+    value = pdist.throughput(vs, world, args.steps, t_e) / 1e6
+    ssfm_value = pdist.throughput(vs, world, k_s, t_s) / 1e6
     launch_s = t_e / args.steps           # one kernel per step
     achieved = BYTES_PER_VSAMPLE * vs / launch_s / 1e9
     peak, peak_kind = hbm_peak()
@@ -225,10 +224,8 @@ def run_ours(args):
     for _ in range(k_e2e):
         pe.run_host(xh, yh)
     barrier()
-    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_value = world * vs * k_e2e / t_e2e.item() / 1e6
+    (t_e2e,) = pdist.max_over_ranks([time.perf_counter() - t0], device="cuda")
+    e2e_value = pdist.throughput(vs, world, k_e2e, t_e2e) / 1e6
 
     batch = None
     if args.batch_jobs > 0:

@@ -46,7 +46,15 @@ extern "C" {
 #define DBP_ZERO       1   /* waveform is zero outside [0, n)                          */
 #define DBP_SSFM       0   /* Eq. 2 nonlinear sub-step (n_taps must be 0)               */
 #define DBP_ESSFM      1   /* Eq. 3 nonlinear sub-step with n_taps = N_c coefficients   */
+#define DBP_FFE        2   /* linear sub-step only: bulk dispersion compensation, the
+                              feed-forward equaliser of Section III (n_taps must be 0)  */
+#define DBP_SCHEME_FUSED    0   /* all N_s steps on chip per block; overlap covers the whole link */
+#define DBP_SCHEME_PER_STEP 1   /* one pass per step through HBM; per-step overlap
+                                   ceil(M_s) + 2 N_c, so short blocks suit long links  */
 #define DBP_FP32       0   /* FFT linear sub-step in FP32                               */
+#define DBP_SPLIT_BF16 1   /* linear sub-step as DFT-matrix GEMMs on the tensor cores,
+                              BF16 hi/lo split operands, FP32 accumulation              */
+#define DBP_SPLIT_FP16 2   /* the same with FP16 hi/lo split operands                  */
 
 /* Opaque stream handle: a cudaStream_t (NULL = legacy default stream). */
 typedef void *dbp_stream_t;
@@ -72,7 +80,7 @@ typedef struct {
 
 /* The backpropagation steps. */
 typedef struct {
-    int32_t method;             /* DBP_SSFM or DBP_ESSFM                                 */
+    int32_t method;             /* DBP_SSFM, DBP_ESSFM or DBP_FFE                        */
     int32_t n_steps;            /* N_s >= 1; step 0 is next to the receiver              */
     int32_t n_taps;             /* N_c, 0..DBP_MAX_TAPS (0 for DBP_SSFM)                 */
     const float  *coeffs;       /* host; c_0..c_Nc: [n_steps][n_taps+1] if
@@ -84,7 +92,10 @@ typedef struct {
     int32_t fft_size;           /* N in {512,1024,2048,4096,8192}                        */
     int32_t overlap;            /* O: 0 = rule ceil(M) + 2 N_s N_c rounded up to a
                                    multiple of 8; else a multiple of 4 in [0, N)        */
-    int32_t precision;          /* DBP_FP32                                              */
+    int32_t precision;          /* DBP_FP32, DBP_SPLIT_BF16 or DBP_SPLIT_FP16            */
+    int32_t dft_block;          /* split precisions: DFT-GEMM size N_a in {64,128,256}
+                                   with fft_size in {1024,2048,4096} and 4 <= N/N_a <= 32  */
+    int32_t scheme;             /* DBP_SCHEME_FUSED or DBP_SCHEME_PER_STEP               */
 } dbp_steps;
 
 #define DBP_MAX_TAPS  64
@@ -93,7 +104,8 @@ typedef struct {
 /* Geometry and step table of a plan, computed on the host. */
 typedef struct {
     int32_t fft_size;           /* N                                                     */
-    int32_t overlap;            /* O (even); O/2 samples discarded at each block end      */
+    int32_t overlap;            /* O (even); O/2 samples discarded at each block end
+                                   (per-step scheme: the largest per-step overlap)       */
     int32_t valid;              /* N - O output samples per block                        */
     int32_t n_blocks;           /* blocks per waveform = ceil(n_samples / valid)         */
     int32_t n_steps;

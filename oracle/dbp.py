@@ -118,3 +118,12 @@ def dbp(r: np.ndarray, cfg: DBPConfig) -> np.ndarray:
     zc = np.moveaxis(zc, -3, -2)                       # [..., 2, nb, V]
     out = zc.reshape(zc.shape[:-2] + (nb * v,))
     return out[..., :n]
+
+
+def dbp_per_step(r: np.ndarray, cfgs) -> np.ndarray:
+    """Per-step-pass scheme: each step is a separate overlap-and-save pass over the whole
+    waveform (one single-step config per step, in order from the receiver)."""
+    x = np.asarray(r, dtype=np.complex128)
+    for cfg in cfgs:
+        x = dbp(x, cfg)
+    return x

@@ -140,3 +140,19 @@ def make_config(link: dict, fs: float, n_steps: int, n_taps: int, fft_size: int,
         essfm = n_taps > 0
     return DBPConfig(beta2=beta2, fs=fs, fft_size=fft_size, overlap=int(overlap), dz=dz,
                      gamma_eff=geff, coeffs=c, boundary=boundary, essfm=essfm)
+
+
+def per_step_configs(link: dict, fs: float, n_steps: int, n_taps: int, fft_size: int, coeffs=None,
+                     boundary="periodic", essfm=None, step_len_m=None, overlap=None, ffe=False):
+    """One single-step DBPConfig per step for the per-step-pass scheme: step s is its own
+    overlap-and-save pass with overlap ceil(M_s) + 2 N_c (M_s the memory of that step's
+    length, Section III), rounded up to a multiple of 8, unless ``overlap`` is given."""
+    full = make_config(link, fs, n_steps, n_taps, fft_size, coeffs=coeffs, overlap=1 << 30, boundary=boundary,
+                       essfm=essfm, step_len_m=step_len_m, gamma_eff=np.zeros(n_steps) if ffe else None)
+    cfgs = []
+    for s in range(n_steps):
+        o = overlap if overlap else overlap_rule(channel_memory(full.beta2, float(full.dz[s]), fs), 1, n_taps)
+        cfgs.append(DBPConfig(beta2=full.beta2, fs=fs, fft_size=fft_size, overlap=int(o), dz=full.dz[s:s + 1],
+                              gamma_eff=full.gamma_eff[s:s + 1], coeffs=full.coeffs[s:s + 1], boundary=boundary,
+                              essfm=full.essfm))
+    return cfgs

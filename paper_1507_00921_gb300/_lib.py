@@ -25,8 +25,11 @@ DBP_NOALLOC_SCRATCH_BYTES = 1 << 20
 DBP_NOALLOC_MAX_STEPS = 64
 
 DBP_PERIODIC, DBP_ZERO = 0, 1
-DBP_SSFM, DBP_ESSFM = 0, 1
+DBP_SSFM, DBP_ESSFM, DBP_FFE = 0, 1, 2
+DBP_SCHEME_FUSED, DBP_SCHEME_PER_STEP = 0, 1
 DBP_FP32 = 0
+DBP_SPLIT_BF16 = 1
+DBP_SPLIT_FP16 = 2
 DBP_MAX_TAPS = 64
 DBP_BATCH_STREAMING = 1
 DBP_MAX_STEPS = 1024
@@ -47,7 +50,8 @@ class dbp_steps(C.Structure):
     _fields_ = [("method", C.c_int32), ("n_steps", C.c_int32), ("n_taps", C.c_int32),
                 ("coeffs", C.POINTER(C.c_float)), ("coeffs_per_step", C.c_int32),
                 ("step_len_m", C.POINTER(C.c_double)), ("gamma_eff", C.POINTER(C.c_double)),
-                ("fft_size", C.c_int32), ("overlap", C.c_int32), ("precision", C.c_int32)]
+                ("fft_size", C.c_int32), ("overlap", C.c_int32), ("precision", C.c_int32),
+                ("dft_block", C.c_int32), ("scheme", C.c_int32)]
 
 
 class dbp_plan_info(C.Structure):

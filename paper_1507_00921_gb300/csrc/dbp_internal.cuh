@@ -65,6 +65,7 @@ struct FwdParams {
     const float2 *twB;      // [N2][N0 N1 / 16] W_{N/16}^{ch k}
     const float2 *tw2;      // [N1][N0] W_{N0 N1}^{n0 k1}
     int prefetch_ahead;     // blocks ahead whose input window is prefetched into L2 (0: off)
+    int linear_only;        // 1: skip the nonlinear sub-step (FFE)
 };
 
 // One job of a batched launch: a plan's parameters with its own input/output buffers.
@@ -86,6 +87,15 @@ struct PlanImpl {
     int taps_stride;
     bool h_shared;            // all steps share one H table
     int prefetch_ahead = -1;  // L2 prefetch distance in blocks (-1: one wave of resident CTAs)
+    int precision = DBP_FP32;
+    int scheme = DBP_SCHEME_FUSED;
+    int user_overlap = 0;
+    void *d_pp = nullptr;     // per-step scheme: intermediate waveform buffer
+    size_t pp_bytes = 0;
+    int dft_block = 0;
+    float2 *d_Hn = nullptr;   // split precisions: H_s / N in natural frequency order
+    float2 *d_Wn = nullptr;   // split precisions: W_N^m
+    uint32_t *d_F = nullptr;  // split precisions: DFT-matrix hi/lo tables
     int device;
     // device tables
     float2 *d_H = nullptr;
@@ -120,6 +130,13 @@ __global__ void build_h_kernel(float2 *H, int N, int n0, int n1, int n2, double 
 __global__ void build_twiddle_kernel(float2 *twA, float2 *twB, float2 *tw2, int N, int n0, int n1, int n2);
 
 struct AdjParams;
+struct GemmParams;
+int launch_gemm_bf16(const GemmParams &, int N, int NA, int n_wave, bool essfm, cudaStream_t);
+int launch_gemm_fp16(const GemmParams &, int N, int NA, int n_wave, bool essfm, cudaStream_t);
+int build_f_tables_bf16(uint32_t *F, int NA);
+int build_f_tables_fp16(uint32_t *F, int NA);
+int launch_gemm_plan(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_t st);
+int build_gemm_tables(PlanImpl &P);
 int launch_adj_512(const AdjParams &, int n_wave, bool essfm, cudaStream_t);
 int launch_adj_1024(const AdjParams &, int n_wave, bool essfm, cudaStream_t);
 int launch_adj_2048(const AdjParams &, int n_wave, bool essfm, cudaStream_t);

@@ -43,6 +43,7 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
         blk.template pass2<true>();
         __syncthreads();
         blk.pass1_inv(v);
+        if (p.linear_only) continue;   // FFE: dispersion compensation only
 
         // ---- nonlinear sub-step
         const float *__restrict__ a = p.taps + p.taps_stride * s;

@@ -105,13 +105,20 @@ static int validate(const dbp_link *link, const dbp_signal *sig, const dbp_steps
         return DBP_ERR_ARG;
     if (!(sig->sample_rate_hz > 0) || sig->n_samples < 1 || sig->n_waveforms < 1) return DBP_ERR_ARG;
     if (sig->boundary != DBP_PERIODIC && sig->boundary != DBP_ZERO) return DBP_ERR_ARG;
-    if (st->method != DBP_SSFM && st->method != DBP_ESSFM) return DBP_ERR_ARG;
+    if (st->method != DBP_SSFM && st->method != DBP_ESSFM && st->method != DBP_FFE) return DBP_ERR_ARG;
+    if (st->scheme != DBP_SCHEME_FUSED && st->scheme != DBP_SCHEME_PER_STEP) return DBP_ERR_ARG;
     if (st->n_steps < 1 || st->n_steps > DBP_MAX_STEPS) return DBP_ERR_ARG;
     if (st->n_taps < 0 || st->n_taps > DBP_MAX_TAPS) return DBP_ERR_ARG;
-    if (st->method == DBP_SSFM && st->n_taps != 0) return DBP_ERR_ARG;
+    if (st->method != DBP_ESSFM && st->n_taps != 0) return DBP_ERR_ARG;
     if (st->coeffs_per_step != 0 && st->coeffs_per_step != 1) return DBP_ERR_ARG;
-    if (st->precision != DBP_FP32) return DBP_ERR_UNSUPPORTED;
+    if (st->precision != DBP_FP32 && st->precision != DBP_SPLIT_BF16 && st->precision != DBP_SPLIT_FP16)
+        return DBP_ERR_ARG;
     if (!supported_n(st->fft_size)) return DBP_ERR_INFEASIBLE;
+    if (st->precision != DBP_FP32) {
+        const int N = st->fft_size, NA = st->dft_block;
+        if (N < 1024 || N > 4096 || (NA != 64 && NA != 128 && NA != 256) || N / NA < 4 || N / NA > 32)
+            return DBP_ERR_UNSUPPORTED;
+    }
     if (st->overlap < 0 || (st->overlap % 4) != 0) return DBP_ERR_ARG;
     if (st->step_len_m)
         for (int s = 0; s < st->n_steps; ++s)
@@ -135,7 +142,8 @@ int describe(const dbp_link *link, const dbp_signal *sig, const dbp_steps *st, d
     for (int s = 0; s < ns; ++s) {
         const double d = st->step_len_m ? st->step_len_m[s] : L / ns;
         const double bot = top - d;
-        const double g = st->gamma_eff ? st->gamma_eff[s] : gamma * profile_integral(alpha, link->span_len_m, bot, top);
+        double g = st->gamma_eff ? st->gamma_eff[s] : gamma * profile_integral(alpha, link->span_len_m, bot, top);
+        if (st->method == DBP_FFE) g = 0.0;   // linear sub-step only
         if (dz) dz[s] = d;
         if (geff) geff[s] = g;
         total += d;
@@ -145,9 +153,20 @@ int describe(const dbp_link *link, const dbp_signal *sig, const dbp_steps *st, d
     const double mem = 2.0 * kPi * fabs(b2) * total * sig->sample_rate_hz * sig->sample_rate_hz;
     int o = st->overlap;
     if (o == 0) {
-        const long long need = (long long)ceil(mem - 1e-9) + 2LL * ns * st->n_taps;
-        o = (int)(((need + 7) / 8) * 8);
+        long long need;
+        if (st->scheme == DBP_SCHEME_PER_STEP) {   // largest per-step overlap ceil(M_s) + 2 N_c
+            need = 0;
+            for (int s = 0; s < ns; ++s) {
+                const double d = st->step_len_m ? st->step_len_m[s] : L / ns;
+                const double ms = 2.0 * kPi * fabs(b2) * d * sig->sample_rate_hz * sig->sample_rate_hz;
+                const long long q = (long long)ceil(ms - 1e-9) + 2LL * st->n_taps;
+                if (q > need) need = q;
+            }
+        } else {
+            need = (long long)ceil(mem - 1e-9) + 2LL * ns * st->n_taps;
+        }
         if (need > 0x3fffffff) return DBP_ERR_INFEASIBLE;
+        o = (int)(((need + 7) / 8) * 8);
     }
     if (o >= st->fft_size) return DBP_ERR_INFEASIBLE;
     const int valid = st->fft_size - o;
@@ -202,6 +221,10 @@ static void release(PlanImpl &P) {
     if (P.d_craw) cudaFree(P.d_craw);
     if (P.d_geff) cudaFree(P.d_geff);
     if (P.d_adj) cudaFree(P.d_adj);
+    if (P.d_Hn) cudaFree(P.d_Hn);
+    if (P.d_Wn) cudaFree(P.d_Wn);
+    if (P.d_F) cudaFree(P.d_F);
+    if (P.d_pp) cudaFree(P.d_pp);
     free(P.step_dz);
     free(P.step_geff);
     free(P.coeffs);
@@ -244,6 +267,20 @@ int build_h_tables(PlanImpl &P) {
                                    n_tables);
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) rc = DBP_ERR_CUDA;
     }
+    if (!rc && P.precision != DBP_FP32) {
+        // natural frequency order for the DFT-GEMM path (the digit map with n0 = N is the identity)
+        if (P.d_Hn && had < n_tables) {
+            cudaFree(P.d_Hn);
+            P.d_Hn = nullptr;
+        }
+        if (!P.d_Hn && dev_alloc((void **)&P.d_Hn, sizeof(float2) * (size_t)N * n_tables)) rc = DBP_ERR_ALLOC;
+        if (!rc) {
+            dim3 g((N + 255) / 256, n_tables);
+            build_h_kernel<<<g, 256>>>(P.d_Hn, N, N, 1, 1, P.info.beta2_s2_per_m, P.signal.sample_rate_hz, d_dz,
+                                       n_tables);
+            if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) rc = DBP_ERR_CUDA;
+        }
+    }
     if (d_dz) cudaFree(d_dz);
     return rc;
 }
@@ -262,6 +299,10 @@ static int make_plan(const dbp_link *link, const dbp_signal *sig, const dbp_step
     P.info = info;
     P.method = st->method;
     P.coeffs_per_step = st->coeffs_per_step;
+    P.precision = st->precision;
+    P.scheme = st->scheme;
+    P.user_overlap = st->overlap;
+    P.dft_block = st->precision == DBP_FP32 ? 0 : st->dft_block;
     P.n_tapblk = st->method == DBP_ESSFM ? tap_blocks(st->n_taps) : 0;
     P.taps_stride = 1 + 8 * P.n_tapblk;
     const int ns = st->n_steps, N = st->fft_size;
@@ -293,6 +334,7 @@ static int make_plan(const dbp_link *link, const dbp_signal *sig, const dbp_step
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess) rc = DBP_ERR_CUDA;
     }
     if (!rc) rc = upload_taps(P, st->coeffs);
+    if (!rc && P.precision != DBP_FP32) rc = build_gemm_tables(P);
     if (rc) {
         release(P);
         delete plan;
@@ -325,9 +367,65 @@ void fill_fwd_params(const PlanImpl &P, FwdParams &p) {
     p.twB = P.d_twB;
     p.tw2 = P.d_tw2;
     p.prefetch_ahead = P.prefetch_ahead;
+    p.linear_only = P.method == DBP_FFE ? 1 : 0;
+}
+
+static int launch_fwd(const FwdParams &p, int N, int n_wave, bool essfm, cudaStream_t st) {
+    switch (N) {
+        case 512: return launch_fwd_512(p, n_wave, essfm, st);
+        case 1024: return launch_fwd_1024(p, n_wave, essfm, st);
+        case 2048: return launch_fwd_2048(p, n_wave, essfm, st);
+        case 4096: return launch_fwd_4096(p, n_wave, essfm, st);
+        case 8192: return launch_fwd_8192(p, n_wave, essfm, st);
+        default: return DBP_ERR_INFEASIBLE;
+    }
+}
+
+// Per-step scheme: one single-step pass per step, each through HBM with the step's own
+// overlap, ping-ponging between `out` and one plan-owned buffer so the last step writes
+// `out`.
+static int launch_per_step(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_t st) {
+    const int N = P.info.fft_size, ns = P.info.n_steps;
+    const size_t bytes = (size_t)2 * P.signal.n_samples * sizeof(float2) * n_wave;
+    PlanImpl &M = const_cast<PlanImpl &>(P);
+    if (ns > 1 && M.pp_bytes < bytes) {
+        if (M.d_pp) cudaFree(M.d_pp);
+        M.d_pp = nullptr;
+        M.pp_bytes = 0;
+        if (dev_alloc(&M.d_pp, bytes)) return DBP_ERR_ALLOC;
+        M.pp_bytes = bytes;
+    }
+    const double fs = P.signal.sample_rate_hz;
+    const void *src = in;
+    for (int s = 0; s < ns; ++s) {
+        void *dst = ((ns - 1 - s) % 2 == 0) ? out : M.d_pp;
+        FwdParams p;
+        fill_fwd_params(P, p);
+        int o = P.user_overlap;
+        if (o == 0) {
+            const double ms = 2.0 * M_PI * fabs(P.info.beta2_s2_per_m) * P.step_dz[s] * fs * fs;
+            const long long q = (long long)ceil(ms - 1e-9) + 2LL * P.info.n_taps;
+            o = (int)(((q + 7) / 8) * 8);
+        }
+        p.in = (const float2 *)src;
+        p.out = (float2 *)dst;
+        p.n_steps = 1;
+        p.valid = N - o;
+        p.half_overlap = o / 2;
+        p.n_blocks = (int)((P.signal.n_samples + p.valid - 1) / p.valid);
+        p.H = P.d_H + (P.h_shared ? 0 : (size_t)N * s);
+        p.h_stride = 0;
+        p.taps = P.d_taps + (size_t)P.taps_stride * s;
+        const int rc = launch_fwd(p, N, n_wave, P.method == DBP_ESSFM, st);
+        if (rc) return rc;
+        src = dst;
+    }
+    return DBP_OK;
 }
 
 int launch(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_t st) {
+    if (P.precision != DBP_FP32) return launch_gemm_plan(P, in, out, n_wave, st);
+    if (P.scheme == DBP_SCHEME_PER_STEP) return launch_per_step(P, in, out, n_wave, st);
     FwdParams p;
     fill_fwd_params(P, p);
     p.in = (const float2 *)in;

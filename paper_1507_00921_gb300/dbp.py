@@ -17,7 +17,9 @@ import numpy as np
 from . import _lib
 
 _BOUNDARY = {"periodic": _lib.DBP_PERIODIC, "zero": _lib.DBP_ZERO}
-_METHOD = {"ssfm": _lib.DBP_SSFM, "essfm": _lib.DBP_ESSFM}
+_METHOD = {"ssfm": _lib.DBP_SSFM, "essfm": _lib.DBP_ESSFM, "ffe": _lib.DBP_FFE}
+_SCHEME = {"fused": _lib.DBP_SCHEME_FUSED, "per_step": _lib.DBP_SCHEME_PER_STEP}
+_PRECISION = {"fp32": _lib.DBP_FP32, "split_bf16": _lib.DBP_SPLIT_BF16, "split_fp16": _lib.DBP_SPLIT_FP16}
 
 
 def _link_struct(link: dict) -> _lib.dbp_link:
@@ -45,7 +47,8 @@ class _Args:
     """ctypes argument structs plus the host arrays they point into (kept alive)."""
 
     def __init__(self, link, fs, n_samples, n_waveforms, boundary, method, n_steps, n_taps, coeffs,
-                 coeffs_per_step, step_len_m, gamma_eff, fft_size, overlap):
+                 coeffs_per_step, step_len_m, gamma_eff, fft_size, overlap, precision="fp32", dft_block=0,
+                 scheme="fused"):
         self.link = _link_struct(link)
         self.signal = _lib.dbp_signal(float(fs), int(n_samples), int(n_waveforms), _BOUNDARY[boundary])
         self.coeffs = None if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float32)
@@ -59,16 +62,16 @@ class _Args:
             int(bool(coeffs_per_step)),
             self.step_len.ctypes.data_as(dp) if self.step_len is not None else dp(),
             self.gamma_eff.ctypes.data_as(dp) if self.gamma_eff is not None else dp(),
-            int(fft_size), int(overlap), _lib.DBP_FP32)
+            int(fft_size), int(overlap), _PRECISION[precision], int(dft_block), _SCHEME[scheme])
 
 
 def describe(link: dict, fs: float, n_samples: int, *, n_waveforms=1, boundary="periodic", method="essfm",
              n_steps=1, n_taps=0, coeffs=None, coeffs_per_step=False, step_len_m=None, gamma_eff=None,
-             fft_size=4096, overlap=0) -> PlanInfo:
+             fft_size=4096, overlap=0, precision="fp32", dft_block=0, scheme="fused") -> PlanInfo:
     """Plan geometry and step table, computed by libdbp on the host (no GPU needed)."""
     lib = _lib.load()
     a = _Args(link, fs, n_samples, n_waveforms, boundary, method, n_steps, n_taps, coeffs, coeffs_per_step,
-              step_len_m, gamma_eff, fft_size, overlap)
+              step_len_m, gamma_eff, fft_size, overlap, precision, dft_block, scheme)
     info = _lib.dbp_plan_info()
     dz = np.zeros(n_steps)
     ge = np.zeros(n_steps)
@@ -85,11 +88,12 @@ class Plan:
 
     def __init__(self, link: dict, fs: float, n_samples: int, *, n_waveforms=1, boundary="periodic",
                  method="essfm", n_steps=1, n_taps=0, coeffs=None, coeffs_per_step=False, step_len_m=None,
-                 gamma_eff=None, fft_size=4096, overlap=0):
+                 gamma_eff=None, fft_size=4096, overlap=0, precision="fp32", dft_block=0, scheme="fused"):
         import torch
         self._lib = _lib.load()
         self._args = _Args(link, fs, n_samples, n_waveforms, boundary, method, n_steps, n_taps, coeffs,
-                           coeffs_per_step, step_len_m, gamma_eff, fft_size, overlap)
+                           coeffs_per_step, step_len_m, gamma_eff, fft_size, overlap, precision, dft_block,
+                           scheme)
         self.n_samples = int(n_samples)
         self.n_waveforms = int(n_waveforms)
         self.method = method
@@ -97,7 +101,8 @@ class Plan:
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.info = describe(link, fs, n_samples, n_waveforms=n_waveforms, boundary=boundary, method=method,
                              n_steps=n_steps, n_taps=n_taps, coeffs=coeffs, coeffs_per_step=coeffs_per_step,
-                             step_len_m=step_len_m, gamma_eff=gamma_eff, fft_size=fft_size, overlap=overlap)
+                             step_len_m=step_len_m, gamma_eff=gamma_eff, fft_size=fft_size, overlap=overlap,
+                             precision=precision, dft_block=dft_block, scheme=scheme)
         h = C.c_void_p()
         rc = self._lib.dbp_plan(C.byref(self._args.link), C.byref(self._args.signal), C.byref(self._args.steps),
                                 C.byref(h))
@@ -296,7 +301,7 @@ def _autograd():
                 coeffs = np.zeros(shape, dtype=np.float32)
                 coeffs[..., 0] = 1.0
             self.plan = plan
-            self.coeffs = torch.nn.Parameter(torch.as_tensor(np.asarray(coeffs, dtype=np.float32)).reshape(shape))
+            self.coeffs = torch.nn.Parameter(torch.tensor(np.array(coeffs, dtype=np.float32)).reshape(shape))
 
         def forward(self, x):
             return DBPFunction.apply(x, self.coeffs, self.plan)

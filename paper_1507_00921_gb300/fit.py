@@ -1,0 +1,54 @@
+"""Fitting the ESSFM coefficients on the GPU (Section IV and its footnote).
+
+Section IV fits the coefficients by minimum MSE against a many-step SSFM output; its
+footnote suggests the MSE between the equalised output symbols and the transmitted
+symbols instead.  ``fit_adam`` does the latter with gradients from libdbp's adjoint:
+loss = mean over symbols and polarizations of |s_hat - s|^2, where s_hat are the
+matched-filtered (root-raised-cosine) output samples at the symbol centres divided
+by one least-squares complex gain per polarization (replacing the butterfly equaliser
+and carrier recovery of the paper's receiver, which correct impairments a synthetic
+link does not have).  The matched filter and gain are torch operations on the DBP
+output; backpropagation itself runs in libdbp (forward kernel and adjoint kernel).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def rrc_matched_response(n: int, sps: int = 2, rolloff: float = 0.1, device="cuda"):
+    """Root-raised-cosine frequency response on the FFT grid of n samples."""
+    import torch
+    f = torch.fft.fftfreq(n, d=1.0 / sps, device=device).abs().double()
+    lo, hi = 0.5 * (1 - rolloff), 0.5 * (1 + rolloff)
+    h = torch.where(f <= lo, torch.ones_like(f), torch.zeros_like(f))
+    band = (f > lo) & (f < hi)
+    h = torch.where(band, torch.sqrt(0.5 * (1 - torch.sin(math.pi * (f - 0.5) / rolloff))), h)
+    return h.float()
+
+
+def symbol_mse(out, symbols, h_mf, sps: int = 2):
+    """MSE of the gain-corrected matched-filter symbols against the transmitted ones."""
+    import torch
+    r = torch.fft.ifft(torch.fft.fft(out, dim=-1) * h_mf, dim=-1)[..., ::sps]
+    g = (torch.conj(symbols) * r).sum(-1, keepdim=True) / (symbols.abs() ** 2).sum(-1, keepdim=True)
+    return ((r / g - symbols).abs() ** 2).mean()
+
+
+def fit_adam(plan, x, symbols, coeffs0=None, n_iter: int = 200, lr: float = 2e-3, sps: int = 2):
+    """Adam on the ESSFM coefficients of ``plan`` for waveforms x [B, 2, n] (CUDA
+    complex64) and transmitted symbols [B, 2, n/sps].  Returns (coeffs, losses)."""
+    import torch
+    from .dbp import DBP
+    module = DBP(plan, coeffs0)
+    opt = torch.optim.Adam(module.parameters(), lr=lr)
+    h_mf = rrc_matched_response(x.shape[-1], sps, device=x.device)
+    losses = []
+    for _ in range(n_iter):
+        opt.zero_grad()
+        loss = symbol_mse(module(x), symbols, h_mf, sps)
+        loss.backward()
+        opt.step()
+        losses.append(float(loss.detach()))
+    return module.coeffs.detach().cpu().numpy().astype(np.float32), losses

@@ -178,3 +178,46 @@ def test_full_size_3200km_sampled_blocks(torch_cuda, method, ns, nc, fft):
             lo, hi = b * v, min((b + 1) * v, n)
             rel_rms, max_rel = compare(got[w][:, lo:hi].astype(np.complex128), ref[j][:, : hi - lo])
             assert rel_rms <= TOL_RMS and max_rel <= TOL_MAX, (w, b, rel_rms, max_rel)
+
+
+SCHEME_CASES = [
+    # id, spans, n, nw, kw  (per-step scheme: one pass per step; FFE: linear sub-step only)
+    ("ffe_3200km_N4096", 40, 2 ** 14 + 5, 2, dict(method="ffe", n_steps=1, fft_size=4096)),
+    ("ffe_800km_N1024_zero", 10, 5000, 1, dict(method="ffe", n_steps=1, fft_size=1024, boundary="zero")),
+    ("perstep_ssfm20_3200km_N512", 40, 6000, 1, dict(method="ssfm", n_steps=20, fft_size=512, scheme="per_step")),
+    ("perstep_ssfm20_3200km_N1024", 40, 2 ** 14, 2, dict(method="ssfm", n_steps=20, fft_size=1024,
+                                                          scheme="per_step")),
+    ("perstep_essfm4_nc16_3200km_N1024", 40, 9000, 1, dict(method="essfm", n_steps=4, n_taps=16, fft_size=1024,
+                                                           scheme="per_step")),
+    ("perstep_essfm3_nc8_nonuniform_N2048_zero", 40, 7000, 1,
+     dict(method="essfm", n_steps=3, n_taps=8, fft_size=2048, scheme="per_step", boundary="zero",
+          step_len_m=np.array([1.0e6, 1.5e6, 0.7e6]))),
+]
+
+
+@pytest.mark.parametrize("case", SCHEME_CASES, ids=[c[0] for c in SCHEME_CASES])
+def test_ffe_and_per_step_scheme(torch_cuda, case):
+    name, spans, n, nw, kw = case
+    link = synth.link(spans)
+    nc = kw.get("n_taps", 0)
+    if nc:
+        c = 0.6 * np.exp(-np.arange(nc + 1) / max(1.0, nc / 3.0))
+        kw = dict(kw, coeffs=(c / (c[0] + 2 * c[1:].sum())).astype(np.float32))
+    x = synth.random_field(nw, n, synth.dbm_to_w(2.0), seed=2000 + len(name))
+    got, info = gpu_dbp(torch_cuda, x, link, **kw)
+    xr = x.astype(np.complex64).astype(np.complex128)
+    coeffs = None if kw.get("coeffs") is None else np.asarray(kw["coeffs"], dtype=np.float32).astype(np.float64)
+    if kw.get("scheme") == "per_step":
+        cfgs = fiber.per_step_configs(link, FS, kw["n_steps"], nc, kw["fft_size"], coeffs=coeffs,
+                                      boundary=kw.get("boundary", "periodic"), essfm=kw["method"] == "essfm",
+                                      step_len_m=kw.get("step_len_m"))
+        assert info.overlap == max(c.overlap for c in cfgs)
+        ref = odbp.dbp_per_step(xr, cfgs)
+    else:
+        cfg = fiber.make_config(link, FS, kw["n_steps"], 0, kw["fft_size"], overlap=info.overlap,
+                                boundary=kw.get("boundary", "periodic"), essfm=False,
+                                gamma_eff=np.zeros(kw["n_steps"]))
+        ref = odbp.dbp(xr, cfg)
+    rel_rms, max_rel = compare(got, ref)
+    print(f"\n{name}: relative RMS error {rel_rms:.3e}, max error / RMS {max_rel:.3e}")
+    assert rel_rms <= TOL_RMS and max_rel <= TOL_MAX, (rel_rms, max_rel)

@@ -296,3 +296,27 @@ def test_linear_adjoint_dot_product():
     lhs = np.vdot(v, ux)            # <v, U x>
     rhs = np.vdot(g_in, r)          # <U^H v, x>
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+# ---------------------------------------------------------------- per-step-pass scheme
+def test_per_step_scheme_full_length_equals_fused():
+    link = synth.link(10)
+    r = crandn((2, 2048), 41) * 0.04
+    fused = fiber.make_config(link, FS, 4, 3, 2048, coeffs=[0.5, 0.2, 0.1, 0.05], overlap=0)
+    cfgs = fiber.per_step_configs(link, FS, 4, 3, 2048, coeffs=[0.5, 0.2, 0.1, 0.05], overlap=0)
+    for c in cfgs:
+        c.overlap = 0
+    assert np.array_equal(dbp.dbp_per_step(r, cfgs), dbp.dbp(r, fused))
+
+
+def test_per_step_scheme_overlap_rule_and_convergence():
+    link = synth.link(40)
+    cfgs = fiber.per_step_configs(link, FS, 20, 0, 512)
+    assert all(c.overlap == 72 for c in cfgs)            # ceil(1367.2 / 20) = 69 -> 72
+    tx, _, _ = synth.pm_qpsk_waveform(2 ** 11, 42, 0.0)
+    r = olink.forward(tx, link, FS, steps_per_span=1, gamma_scale=0.0)
+    errs = []
+    for o in (72, 160, 320):
+        c = fiber.per_step_configs(link, FS, 20, 0, 1024, overlap=o, ffe=True)
+        errs.append(rel(dbp.dbp_per_step(r, c), tx))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-3
