@@ -71,6 +71,25 @@ __device__ __forceinline__ float2 expj(float th) {
 #endif
 }
 
+// TF32 helpers for the tensor-core filter: x = hi + lo with both parts TF32-rounded
+// (about 22 significant bits together).
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 __device__ __forceinline__ float joint_intensity(float2 y0, float2 y1) {
     return fmaf(y0.x, y0.x, fmaf(y0.y, y0.y, fmaf(y1.x, y1.x, y1.y * y1.y)));
 }
@@ -333,6 +352,72 @@ struct Blk {
         for (int q = 0; q < 4; ++q) pt[q] = make_float4(th[4 * q], th[4 * q + 1], th[4 * q + 2], th[4 * q + 3]);
     }
 
+    // The same filter on the tensor cores, for all N positions of the block: with
+    // NCP = 8 n_tapblk taps a side, output group q (positions 16q..16q+15) is
+    //   theta[16q + r] = sum_u W[q][u] B[u][r],  W[q][u] = src[16q - NCP + u] (circular),
+    //   B[u][r] = a_|u - NCP - r| inside the band |u - NCP - r| <= NCP, else 0,
+    // a (groups x (16 + 2 NCP)) by ((16 + 2 NCP) x 16) matrix product computed with
+    // mma.sync m16n8k8 in TF32 with both operands split hi + lo (three products,
+    // FP32 accumulation, ~2^-21 relative per term).  Each warp owns two tiles of 16
+    // groups; the B fragments are formed from the taps and shared by both tiles.
+    // Selected with DBP_FIR_TC; on GB300 the register FMA filter (fir16) measured faster
+    // inside the fused kernel (3200 km ESSFM-1, N_c = 32: 49.7 vs 41.6 G samples/s).
+    __device__ __forceinline__ void fir_tc(const float *src, float *dst, const float *__restrict__ a,
+                                           int n_tapblk) const {
+        const int lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
+        const int ncp = 8 * n_tapblk;
+        const int ksteps = 2 + 2 * n_tapblk;            // (16 + 2 NCP) / 8
+        float c[2][2][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) c[i][j][k] = 0.f;
+        for (int ks = 0; ks < ksteps; ++ks) {
+            uint32_t bh[2][2], bl[2][2];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int d = 8 * ks + tq + 4 * h - ncp - (8 * nt + g);
+                    const int ad = d < 0 ? -d : d;
+                    const float coef = ad <= ncp ? __ldg(a + ad) : 0.f;
+                    split_tf32(coef, bh[nt][h], bl[nt][h]);
+                }
+#pragma unroll
+            for (int tile = 0; tile < 2; ++tile) {
+                const int q0 = (2 * warp + tile) * 16 + g;
+                const int e0 = 16 * q0 - ncp + 8 * ks + tq;
+                const float w0 = src[pphys(e0 & (N - 1))];
+                const float w1 = src[pphys((e0 + 128) & (N - 1))];
+                const float w2 = src[pphys((e0 + 4) & (N - 1))];
+                const float w3 = src[pphys((e0 + 132) & (N - 1))];
+                uint32_t ah[4], al[4];
+                split_tf32(w0, ah[0], al[0]);
+                split_tf32(w1, ah[1], al[1]);
+                split_tf32(w2, ah[2], al[2]);
+                split_tf32(w3, ah[3], al[3]);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    mma_tf32(c[tile][nt], ah, bh[nt][0], bh[nt][1]);
+                    mma_tf32(c[tile][nt], ah, bl[nt][0], bl[nt][1]);
+                    mma_tf32(c[tile][nt], al, bh[nt][0], bh[nt][1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int tile = 0; tile < 2; ++tile)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int q0 = (2 * warp + tile) * 16 + g;
+                const int r = 8 * nt + 2 * tq;
+                *reinterpret_cast<float2 *>(dst + pphys(16 * q0 + r)) = make_float2(c[tile][nt][0], c[tile][nt][1]);
+                *reinterpret_cast<float2 *>(dst + pphys(16 * (q0 + 8) + r)) =
+                    make_float2(c[tile][nt][2], c[tile][nt][3]);
+            }
+    }
+
     // ESSFM phase theta (Eq. 3) of the block in registers, into farr(1).  The block
     // buffer must be free (a barrier after the last pass-1' read); returns after a
     // barrier, with theta visible to all threads.
@@ -343,7 +428,11 @@ struct Blk {
 #pragma unroll
             for (int j = 0; j < N2; ++j) sP[pphys(pos1(i, j))] = joint_intensity(v[0][i][j], v[1][i][j]);
         __syncthreads();
+#ifdef DBP_FIR_TC
+        fir_tc(sP, farr(1), a, n_tapblk);
+#else
         fir16(sP, farr(1), a, n_tapblk);
+#endif
         __syncthreads();
     }
 };
