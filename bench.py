@@ -231,6 +231,8 @@ def run_ours(args):
     if args.batch_jobs > 0:
         batch = batch_measure(torch, args.batch_jobs, 5, stream)
     fp32 = fp32_pipe(value / world, fft_e, pe.info.overlap)
+    precision = precision_measure(torch, stream) if not args.no_extras else None
+    adjoint = adjoint_measure(torch, stream) if not args.no_extras else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds, fft_e)
@@ -256,6 +258,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(x_host.nbytes), "steps": k_e2e},
             "fp32_pipe": fp32,
             "batch": batch,
+            "precision_variants": precision,
+            "adjoint": adjoint,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -333,6 +337,62 @@ def batch_measure(torch, n_jobs: int, reps: int, stream):
             "one_by_one": round(total / t_seq / 1e6, 1), "speedup": round(t_seq / t_batch, 3), "status": status,
             "block_lengths": {f"{k[0] * 80}km_{k[1]}": v for k, v in sorted(tuned.items())},
             "launches": "1 CUDA graph launch (persistent kernel per block length)"}
+
+
+def time_plan(torch, fn, stream, reps=10):
+    with torch.cuda.stream(stream):
+        fn()
+        fn()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def precision_measure(torch, stream):
+    """800 km single-step ESSFM (N_c = 16, N = 1024) on 256 waveforms of 2^14 symbols:
+    FP32 FFT path vs the split FP16 / BF16 DFT-GEMM paths (N_a = 64)."""
+    from paper_1507_00921_gb300 import Plan
+    n, nw = 2 ** 15, 256
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.BASE_SEED + 3)
+    x = torch.randn((nw, 2, n), dtype=torch.complex64, device="cuda", generator=gen) * math.sqrt(
+        synth.dbm_to_w(2.0))
+    y = torch.empty_like(x)
+    out = {}
+    for prec, na in (("fp32", 0), ("split_fp16", 64), ("split_bf16", 64)):
+        with Plan(synth.link(10), synth.SAMPLE_RATE, n, n_waveforms=nw, method="essfm", n_steps=1, n_taps=16,
+                  coeffs=essfm_coeffs(16), fft_size=1024, precision=prec, dft_block=na) as plan:
+            t = time_plan(torch, lambda: plan.run(x, y, stream=stream), stream)
+        out[prec] = round(nw * n / t / 1e6, 1)
+    out["workload"] = "800 km ESSFM N_s=1 N_c=16, N=1024, N_a=64, 256 x 2^15 samples"
+    out["unit"] = UNIT
+    return out
+
+
+def adjoint_measure(torch, stream):
+    """Reverse mode (forward + adjoint kernels) over 3200 km: 64 waveforms of 2^16
+    symbols, ESSFM N_c = 16, N_s in {1, 2, 4}, N = 4096."""
+    from paper_1507_00921_gb300 import Plan
+    n, nw = 2 ** 17, 64
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.BASE_SEED + 4)
+    x = torch.randn((nw, 2, n), dtype=torch.complex64, device="cuda", generator=gen) * math.sqrt(
+        synth.dbm_to_w(2.0))
+    g = torch.randn((nw, 2, n), dtype=torch.complex64, device="cuda", generator=gen)
+    out = {}
+    for ns in (1, 2, 4):
+        with Plan(synth.link(N_SPANS), synth.SAMPLE_RATE, n, n_waveforms=nw, method="essfm", n_steps=ns,
+                  n_taps=16, coeffs=essfm_coeffs(16), fft_size=4096) as plan:
+            t = time_plan(torch, lambda: plan.grad(x, g, stream=stream), stream, reps=5)
+        out[f"n_steps_{ns}"] = round(nw * n / t / 1e6, 1)
+    out["workload"] = "3200 km ESSFM N_c=16, N=4096, 64 x 2^17 samples, input + coefficient + gamma + dz gradients"
+    out["unit"] = UNIT
+    return out
 
 
 def fp32_pipe(value_msps: float, fft: int, overlap: int):
@@ -419,6 +479,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-jobs", type=int, default=256, help="uneven batched workload size (0: skip)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the precision-variant and adjoint lines")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

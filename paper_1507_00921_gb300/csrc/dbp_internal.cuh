@@ -116,8 +116,8 @@ struct PlanImpl {
     void *d_stage_in = nullptr;
     void *d_stage_out = nullptr;
     size_t stage_bytes = 0;
-    cudaStream_t aux[2] = {nullptr, nullptr};
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 // Planner pieces shared by the entry points (plan.cu).

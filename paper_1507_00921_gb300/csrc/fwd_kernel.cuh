@@ -89,21 +89,28 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
         }
 }
 
+// Persistent over blocks: CTA c processes blocks c, c + gridDim.x, ...  The twiddle
+// tables (and H when all steps share it) are loaded into shared memory once per CTA;
+// the input window of the block this CTA runs next is prefetched into L2 while the
+// current one is processed.
 template <int N, bool ESSFM>
-__global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const FwdParams p) {
+__global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const FwdParams p, int total) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Blk<N> blk(smem_raw, threadIdx.x);
-    const int w = blockIdx.x / p.n_blocks;
-    const int b = blockIdx.x - w * p.n_blocks;
-    blk.prefetch_h(p.H);
     blk.load_tables(p.twA, p.twB, p.tw2);
-    if (p.prefetch_ahead > 0 && blockIdx.x + p.prefetch_ahead < gridDim.x) {
-        const unsigned nb = blockIdx.x + p.prefetch_ahead;
-        const int w2 = nb / p.n_blocks, b2 = nb - w2 * p.n_blocks;
-        blk.prefetch_window_l2(p.in + (size_t)w2 * 2 * p.n, p.n, (long long)b2 * p.valid - p.half_overlap);
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int w = item / p.n_blocks;
+        const int b = item - w * p.n_blocks;
+        if (item == (int)blockIdx.x || p.h_stride != 0) blk.prefetch_h(p.H);
+        const int next = item + (int)gridDim.x;
+        if (p.prefetch_ahead != 0 && next < total) {
+            const int w2 = next / p.n_blocks, b2 = next - w2 * p.n_blocks;
+            blk.prefetch_window_l2(p.in + (size_t)w2 * 2 * p.n, p.n, (long long)b2 * p.valid - p.half_overlap);
+        }
+        __syncthreads();   // tables visible; previous block's shared-memory use finished
+        process_block<N, ESSFM>(p, blk, w, b);
+        __syncthreads();
     }
-    __syncthreads();   // twiddle tables visible
-    process_block<N, ESSFM>(p, blk, w, b);
 }
 
 // SMs x resident CTAs per SM for a kernel configuration (at least 1).
@@ -127,18 +134,19 @@ int launch_fwd_n(const FwdParams &p, int n_wave, bool essfm, cudaStream_t st) {
     static int resident[64][2];   // CTAs resident per GPU (SMs x CTAs per SM), per device and variant
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DBP_ERR_CUDA;
-    FwdParams q = p;
+    const int v = essfm ? 1 : 0;
     if (essfm) {
         if (!set_smem_once(dbp_fwd_kernel<N, true>, G::SMEM, done_essfm)) return DBP_ERR_CUDA;
-        if (!resident[dev][1]) resident[dev][1] = resident_ctas(dbp_fwd_kernel<N, true>, G::T, G::SMEM);
-        if (q.prefetch_ahead < 0) q.prefetch_ahead = resident[dev][1];
-        dbp_fwd_kernel<N, true><<<(unsigned)grid, G::T, G::SMEM, st>>>(q);
+        if (!resident[dev][v]) resident[dev][v] = resident_ctas(dbp_fwd_kernel<N, true>, G::T, G::SMEM);
     } else {
         if (!set_smem_once(dbp_fwd_kernel<N, false>, G::SMEM, done_ssfm)) return DBP_ERR_CUDA;
-        if (!resident[dev][0]) resident[dev][0] = resident_ctas(dbp_fwd_kernel<N, false>, G::T, G::SMEM);
-        if (q.prefetch_ahead < 0) q.prefetch_ahead = resident[dev][0];
-        dbp_fwd_kernel<N, false><<<(unsigned)grid, G::T, G::SMEM, st>>>(q);
+        if (!resident[dev][v]) resident[dev][v] = resident_ctas(dbp_fwd_kernel<N, false>, G::T, G::SMEM);
     }
+    const int ctas = (int)(grid < resident[dev][v] ? grid : resident[dev][v]);
+    if (essfm)
+        dbp_fwd_kernel<N, true><<<(unsigned)ctas, G::T, G::SMEM, st>>>(p, (int)grid);
+    else
+        dbp_fwd_kernel<N, false><<<(unsigned)ctas, G::T, G::SMEM, st>>>(p, (int)grid);
     return cudaGetLastError() == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
 }
 

@@ -500,9 +500,9 @@ int dbp_run_host(dbp_plan_t *plan, const void *in, void *out, dbp_stream_t strea
         for (auto &e : P.ev)
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return DBP_ERR_CUDA;
     }
-    // Pipeline: chunks of waveforms alternate between two streams so that the copy in of
-    // one chunk, the kernel of another and the copy out of a third overlap.
-    const int chunks = nw >= 8 ? 8 : nw;
+    // Pipeline: chunks of waveforms rotate over three streams, so that the copy in of one
+    // chunk, the kernel of the previous one and the copy out of the one before overlap.
+    const int chunks = nw >= 24 ? 24 : nw;
     if (cudaEventRecord(P.ev[0], st) != cudaSuccess) return DBP_ERR_CUDA;
     for (auto &s : P.aux)
         if (cudaStreamWaitEvent(s, P.ev[0], 0) != cudaSuccess) return DBP_ERR_CUDA;
@@ -511,7 +511,7 @@ int dbp_run_host(dbp_plan_t *plan, const void *in, void *out, dbp_stream_t strea
         const int w1 = (int)(((long long)nw * (c + 1)) / chunks);
         const int cnt = w1 - w0;
         if (cnt <= 0) continue;
-        cudaStream_t s = P.aux[c & 1];
+        cudaStream_t s = P.aux[c % 3];
         const size_t off = wb * w0, len = wb * cnt;
         if (cudaMemcpyAsync((char *)P.d_stage_in + off, (const char *)in + off, len, cudaMemcpyHostToDevice, s) !=
             cudaSuccess)
@@ -523,10 +523,10 @@ int dbp_run_host(dbp_plan_t *plan, const void *in, void *out, dbp_stream_t strea
             return DBP_ERR_CUDA;
         w0 = w1;
     }
-    if (cudaEventRecord(P.ev[1], P.aux[0]) != cudaSuccess || cudaEventRecord(P.ev[2], P.aux[1]) != cudaSuccess)
-        return DBP_ERR_CUDA;
-    if (cudaStreamWaitEvent(st, P.ev[1], 0) != cudaSuccess || cudaStreamWaitEvent(st, P.ev[2], 0) != cudaSuccess)
-        return DBP_ERR_CUDA;
+    for (int k = 0; k < 3; ++k) {
+        if (cudaEventRecord(P.ev[1 + k], P.aux[k]) != cudaSuccess) return DBP_ERR_CUDA;
+        if (cudaStreamWaitEvent(st, P.ev[1 + k], 0) != cudaSuccess) return DBP_ERR_CUDA;
+    }
     return cudaStreamSynchronize(st) == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
 }
 
