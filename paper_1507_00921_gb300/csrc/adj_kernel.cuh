@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(Geo<N>::T, 1) dbp_adj_kernel(const AdjParams q
         const float *__restrict__ a = p.taps + p.taps_stride * s;
         if constexpr (ESSFM) {
             __syncthreads();
-            blk.essfm_theta(v, a, p.n_tapblk);
+            blk.stage_taps(a, p.taps_stride);
+            blk.essfm_theta(v, blk.sa, p.n_tapblk);
         }
         const float a0 = __ldg(a);
         float4 *ck = q.ckpt + ((size_t)blkid * (ns - 1) + s) * N;
@@ -244,7 +245,8 @@ __global__ void __launch_bounds__(Geo<N>::T, 1) dbp_adj_kernel(const AdjParams q
         float *rp = part + s * q.nr;
         if constexpr (ESSFM) {
             __syncthreads();
-            blk.essfm_theta(v, a, p.n_tapblk);
+            blk.stage_taps(a, p.taps_stride);
+            blk.essfm_theta(v, blk.sa, p.n_tapblk);
             float *sS = blk.farr(2);
             const float *sT = blk.farr(1);
 #pragma unroll
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(Geo<N>::T, 1) dbp_adj_kernel(const AdjParams q
                     }
                     block_sum<N, 8>(acc, red, rp + 1 + i0, t);
                 }
-                blk.fir16(sS, blk.farr(1), a, p.n_tapblk);
+                blk.fir16(sS, blk.farr(1), blk.sa, p.n_tapblk);
             }
             __syncthreads();
             const float *sD = blk.farr(1);

@@ -107,6 +107,7 @@ struct Blk {
     float2 *sA;
     float2 *sB;
     float2 *s2;
+    float *sa;     // current step's taps gamma_eff c_i (shared, broadcast reads)
     int t;
 
     __device__ __forceinline__ Blk(unsigned char *smem, int tid)
@@ -115,7 +116,13 @@ struct Blk {
           sA(reinterpret_cast<float2 *>(smem + G::OFF_TWA)),
           sB(reinterpret_cast<float2 *>(smem + G::OFF_TWB)),
           s2(reinterpret_cast<float2 *>(smem + G::OFF_TW2)),
+          sa(reinterpret_cast<float *>(smem + G::OFF_TAPS)),
           t(tid) {}
+
+    // Stages one step's taps (n floats) in shared memory; visible after the next barrier.
+    __device__ __forceinline__ void stage_taps(const float *__restrict__ a, int n) {
+        for (int i = t; i < n; i += T) sa[i] = __ldg(a + i);
+    }
 
     // float views of the block buffer for the nonlinear sub-step (valid while the block
     // is in registers): k = 0 joint intensity, 1 phase, 2 (adjoint) phase gradient.
@@ -312,13 +319,12 @@ struct Blk {
     // Symmetric filter over 16 consecutive positions 16t..16t+15 (circular in the block):
     // out_k = a_0 src_k + sum_{i=1}^{8 n_tapblk} a_i (src_{k-i} + src_{k+i}), read from
     // the float array src and written to dst (both pphys-indexed).  Eq. 3 when src = P.
-    __device__ __forceinline__ void fir16(const float *src, float *dst, const float *__restrict__ a,
-                                          int n_tapblk) const {
+    __device__ __forceinline__ void fir16(const float *src, float *dst, const float *a, int n_tapblk) const {
         const int k0 = 16 * t;
         float th[16];
         {
             const float4 *pc = reinterpret_cast<const float4 *>(src + pphys(k0));
-            const float a0 = __ldg(a);
+            const float a0 = a[0];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float4 f = pc[q];
@@ -342,7 +348,7 @@ struct Blk {
             }
 #pragma unroll
             for (int ii = 1; ii <= 8; ++ii) {
-                const float ai = __ldg(a + i0 + ii);
+                const float ai = a[i0 + ii];
 #pragma unroll
                 for (int r = 0; r < 16; ++r) th[r] = fmaf(ai, lw[r - ii + 8] + rw[r + ii], th[r]);
             }
@@ -362,8 +368,7 @@ struct Blk {
     // groups; the B fragments are formed from the taps and shared by both tiles.
     // Selected with DBP_FIR_TC; on GB300 the register FMA filter (fir16) measured faster
     // inside the fused kernel (3200 km ESSFM-1, N_c = 32: 49.7 vs 41.6 G samples/s).
-    __device__ __forceinline__ void fir_tc(const float *src, float *dst, const float *__restrict__ a,
-                                           int n_tapblk) const {
+    __device__ __forceinline__ void fir_tc(const float *src, float *dst, const float *a, int n_tapblk) const {
         const int lane = t & 31, warp = t >> 5, g = lane >> 2, tq = lane & 3;
         const int ncp = 8 * n_tapblk;
         const int ksteps = 2 + 2 * n_tapblk;            // (16 + 2 NCP) / 8
@@ -382,7 +387,7 @@ struct Blk {
                 for (int h = 0; h < 2; ++h) {
                     const int d = 8 * ks + tq + 4 * h - ncp - (8 * nt + g);
                     const int ad = d < 0 ? -d : d;
-                    const float coef = ad <= ncp ? __ldg(a + ad) : 0.f;
+                    const float coef = ad <= ncp ? a[ad] : 0.f;
                     split_tf32(coef, bh[nt][h], bl[nt][h]);
                 }
 #pragma unroll
@@ -421,7 +426,7 @@ struct Blk {
     // ESSFM phase theta (Eq. 3) of the block in registers, into farr(1).  The block
     // buffer must be free (a barrier after the last pass-1' read); returns after a
     // barrier, with theta visible to all threads.
-    __device__ __forceinline__ void essfm_theta(const Regs &v, const float *__restrict__ a, int n_tapblk) {
+    __device__ __forceinline__ void essfm_theta(const Regs &v, const float *a, int n_tapblk) {
         float *sP = farr(0);
 #pragma unroll
         for (int i = 0; i < C1; ++i)

@@ -13,7 +13,8 @@ namespace dbp {
 // Shared memory (bytes): the block with both polarizations interleaved, one float4
 // (x_pol0, x_pol1) per position plus one float4 of padding per N0 positions; the step's
 // H table; the split first-pass twiddles W_N^{c k} = A[c mod 16][k] * B[c div 16][k];
-// the second-pass twiddles.  The ESSFM intensity P and phase theta arrays reuse the
+// the second-pass twiddles; the current step's filter taps.  The ESSFM intensity P and
+// phase theta arrays reuse the
 // block buffer while the block is held in registers.
 template <int N>
 struct Geo {
@@ -32,7 +33,9 @@ struct Geo {
     static constexpr size_t OFF_TWA = OFF_H + (size_t)PADH * 8;
     static constexpr size_t OFF_TWB = OFF_TWA + (size_t)TWA * 8;
     static constexpr size_t OFF_TW2 = OFF_TWB + (size_t)TWB * 8;
-    static constexpr size_t SMEM = OFF_TW2 + (size_t)TW2 * 8;
+    static constexpr size_t OFF_TAPS = OFF_TW2 + (size_t)TW2 * 8;
+    static constexpr int TAPS_MAX = 1 + DBP_MAX_TAPS + 15;   // one step's taps, 8-padded
+    static constexpr size_t SMEM = OFF_TAPS + (size_t)TAPS_MAX * 4;
     static constexpr int MINB = (512 / T) > 0 ? (512 / T) : 1;
     static_assert(2 * PADP * 4 <= PADX * 16, "P/theta must fit in the block buffer");
     static_assert(SMEM <= 227 * 1024, "shared memory budget");

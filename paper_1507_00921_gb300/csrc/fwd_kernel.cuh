@@ -31,7 +31,8 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
 
     MidMulH<N> mid{blk.sH};
     for (int s = 0; s < p.n_steps; ++s) {
-        if (ESSFM && s > 0) __syncthreads();   // previous step's theta reads are done
+        if (ESSFM && s > 0) __syncthreads();   // previous step's theta and tap reads are done
+        if (ESSFM) blk.stage_taps(p.taps + p.taps_stride * s, p.taps_stride);
         blk.pass1_fwd(v);
         __syncthreads();
         blk.template pass2<false>();
@@ -49,7 +50,7 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
         const float *__restrict__ a = p.taps + p.taps_stride * s;
         if constexpr (ESSFM) {
             __syncthreads();   // block buffer free: P and theta reuse it
-            blk.essfm_theta(v, a, p.n_tapblk);
+            blk.essfm_theta(v, blk.sa, p.n_tapblk);
             const float *sT = blk.farr(1);
 #pragma unroll
             for (int i = 0; i < B::C1; ++i)
