@@ -40,6 +40,7 @@ extern "C" {
 #define DBP_ERR_ALIAS       -6   /* output buffer overlaps the input buffer           */
 #define DBP_ERR_UNSUPPORTED -7   /* option not available in this build                */
 #define DBP_ERR_SCRATCH     -8   /* dbp_run_noalloc: problem exceeds its fixed scratch */
+#define DBP_ERR_SINGULAR    -9   /* dbp_fit_coeffs: normal equations not positive definite */
 
 /* Enumerations. */
 #define DBP_PERIODIC   0   /* waveform is periodic outside [0, n) (circular channel)  */
@@ -181,6 +182,33 @@ int dbp_grad(dbp_plan_t *plan, const void *in, const void *grad_out, void *grad_
  * The overlap and block geometry are not changed.  Synchronizes the device.
  */
 int dbp_set_steps(dbp_plan_t *plan, const double *step_len_m, const double *gamma_eff);
+
+/*
+ * Least-squares fit of a single-step ESSFM's coefficients (Section IV: the coefficients
+ * minimise the mean square error between the ESSFM output and a target, e.g. the output
+ * of a many-step SSFM, over a training part of the waveform).  The plan must be ESSFM
+ * with n_steps = 1, FP32 precision and the fused scheme (else DBP_ERR_UNSUPPORTED); its
+ * block geometry, H and gamma_eff are used as they are, its coefficients are not changed
+ * (apply the result with dbp_set_coeffs).
+ *   x, target  DEVICE complex64 [n_waveforms][2][n_samples]: the received waveforms and
+ *              the targets for the plan's outputs.
+ *   n_train    output samples [0, n_train) of every waveform enter the fit (<= 0: all).
+ *   max_iter   Gauss-Newton updates at most (>= 0); tol: stop once every update of c
+ *              is at most tol * max(1, max_i |c_i|).
+ *   coeffs     HOST double [n_taps + 1]: the start point on entry (c = 1, 0, ..., 0 is
+ *              the SSFM), the fitted c_0..c_Nc on return (unscaled: theta = gamma_eff *
+ *              sum_i c_i S_i).
+ *   loss       HOST double [max_iter + 1] or NULL: mean over training vector samples of
+ *              |t_k - z_k|^2 (both polarizations) at the start and after each update.
+ *   n_iter     HOST int or NULL: updates made.
+ * Uses the scratch of dbp_grad (allocated on first use); synchronizes `stream`.  The
+ * normal matrix sum_k P_k S_k S_k^T does not depend on c: it is built once on the GPU
+ * and factored once; each iteration is one GPU pass over the training samples.
+ * Deterministic (fixed-order FP64 reductions).  DBP_ERR_SINGULAR when the normal matrix
+ * is not positive definite (e.g. an all-zero input).
+ */
+int dbp_fit_coeffs(dbp_plan_t *plan, const void *x, const void *target, long long n_train, int max_iter,
+                   double tol, double *coeffs, double *loss, int *n_iter, dbp_stream_t stream);
 
 /*
  * As dbp_run, but in and out are HOST pointers (pinned or pageable).  The plan

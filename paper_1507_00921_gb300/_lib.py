@@ -21,6 +21,7 @@ DBP_ERR_TIMEOUT = -5
 DBP_ERR_ALIAS = -6
 DBP_ERR_UNSUPPORTED = -7
 DBP_ERR_SCRATCH = -8
+DBP_ERR_SINGULAR = -9
 DBP_NOALLOC_SCRATCH_BYTES = 1 << 20
 DBP_NOALLOC_MAX_STEPS = 64
 
@@ -78,6 +79,8 @@ _PROTOS = {
     "dbp_run_host": (C.c_int, [_P, _P, _P, _P]),
     "dbp_grad": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "dbp_set_steps": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "dbp_fit_coeffs": (C.c_int, [_P, _P, _P, C.c_longlong, C.c_int, C.c_double, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_int), _P]),
     "dbp_run_noalloc": (C.c_int, [C.POINTER(dbp_link), C.POINTER(dbp_signal), C.POINTER(dbp_steps), _P, _P, _P]),
     "dbp_destroy": (None, [_P]),
     "dbp_batch_create": (C.c_int, [C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.c_int, C.c_int, C.c_int,

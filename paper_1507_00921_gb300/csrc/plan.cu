@@ -552,6 +552,7 @@ const char *dbp_strerror(int code) {
         case DBP_ERR_ALIAS: return "output buffer overlaps input buffer";
         case DBP_ERR_UNSUPPORTED: return "unsupported option";
         case DBP_ERR_SCRATCH: return "problem exceeds the fixed scratch of dbp_run_noalloc";
+        case DBP_ERR_SINGULAR: return "normal equations of the fit are not positive definite";
         default: return "unknown error";
     }
 }

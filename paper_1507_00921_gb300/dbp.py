@@ -187,6 +187,32 @@ class Plan:
         if ge is not None:
             self.info.step_gamma_eff = ge.copy()
 
+    def fit_coeffs(self, x, target, n_train=None, max_iter: int = 20, tol: float = 1e-12, coeffs0=None,
+                   stream=None):
+        """Section IV least-squares fit of this single-step ESSFM plan's coefficients
+        against ``target`` (same layout as ``x``; e.g. a many-step SSFM output), over the
+        first ``n_train`` output samples of every waveform.  Gauss-Newton from ``coeffs0``
+        (default the SSFM, c = 1, 0, ..., 0).  Returns ``(coeffs float64 [n_taps + 1],
+        losses)``, losses the mean |t - z|^2 per training vector sample at the start and
+        after each update.  The plan's own coefficients are not changed."""
+        import torch
+        self._check_tensor(x, "x")
+        self._check_tensor(target, "target")
+        k = self.info.n_taps + 1
+        c = np.zeros(k, dtype=np.float64)
+        c[0] = 1.0
+        if coeffs0 is not None:
+            c[:] = np.asarray(coeffs0, dtype=np.float64).reshape(k)
+        losses = np.zeros(max_iter + 1, dtype=np.float64)
+        n_iter = C.c_int(0)
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        dp = C.POINTER(C.c_double)
+        rc = self._lib.dbp_fit_coeffs(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(target.data_ptr()),
+                                      int(n_train or 0), int(max_iter), float(tol), c.ctypes.data_as(dp),
+                                      losses.ctypes.data_as(dp), C.byref(n_iter), C.c_void_p(st.cuda_stream))
+        _lib.check(rc, "dbp_fit_coeffs")
+        return c, [float(v) for v in losses[:n_iter.value + 1]]
+
     def set_coeffs(self, coeffs):
         c = np.ascontiguousarray(coeffs, dtype=np.float32)
         rc = self._lib.dbp_set_coeffs(self._h, c.ctypes.data_as(C.POINTER(C.c_float)))

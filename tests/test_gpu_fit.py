@@ -41,3 +41,70 @@ def test_adam_fit_through_adjoint_improves_q():
         qs[name] = rx.evaluate(out.astype(np.complex128), sym, bits)["q_db"]
     print(f"\nloss {losses[0]:.4f} -> {losses[-1]:.4f}; test Q start {qs['start']:.2f} dB, fitted {qs['fitted']:.2f} dB")
     assert qs["fitted"] > qs["start"] + 0.1
+
+
+
+def _mse(out, target, n_train):
+    d = np.asarray(out)[:, :n_train] - np.asarray(target)[:, :n_train]
+    return float(np.mean(np.sum(np.abs(d) ** 2, axis=0)))
+
+
+@pytest.mark.parametrize("nc,fft,n_train", [(8, 1024, None), (4, 512, 5000), (16, 2048, None)])
+def test_gauss_newton_fit_on_gpu_matches_oracle_fit(nc, fft, n_train):
+    """Section IV fit (minimum MSE against a 40-step SSFM target) through dbp_fit_coeffs
+    vs the FP64 oracle's Gauss-Newton fit on the same data: the coefficients agree, the
+    fitted MSE (evaluated by the oracle) is the oracle's optimum, and the reported loss
+    trajectory is the oracle's MSE at the start point and at the result."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import dbp as odbp
+    from oracle import fiber
+    from oracle import fit as ofit
+    from paper_1507_00921_gb300.fit import fit_gauss_newton
+    link = synth.link(10)
+    tx, _, _ = synth.pm_qpsk_waveform(2 ** 13, synth.BASE_SEED + 990, 2.0)
+    r = olink.forward(tx, link, FS, steps_per_span=20, ase_seed=synth.BASE_SEED + 991)
+    r32 = r.astype(np.complex64)
+    target = odbp.dbp(r32.astype(np.complex128), fiber.make_config(link, FS, 40, 0, 2048))
+    n = r.shape[-1]
+    m = n if n_train is None else n_train
+    c_gpu, losses = fit_gauss_newton(link, FS, torch.from_numpy(r32).cuda(),
+                                     torch.from_numpy(target.astype(np.complex64)).cuda(), nc, fft,
+                                     n_train=n_train)
+    cfg = fiber.make_config(link, FS, 1, nc, fft)
+    c_ref = ofit.fit_single_step(r32.astype(np.complex128), target, cfg, n_train=n_train)
+    rin = r32.astype(np.complex128)
+    mse_start = _mse(odbp.dbp(rin, cfg), target, m)
+    mse_ref = _mse(odbp.dbp(rin, fiber.make_config(link, FS, 1, nc, fft, coeffs=c_ref)), target, m)
+    mse_gpu = _mse(odbp.dbp(rin, fiber.make_config(link, FS, 1, nc, fft, coeffs=c_gpu)), target, m)
+    print(f"\nN_c={nc} N={fft}: GPU fit {np.round(c_gpu[:4], 5)}, oracle {np.round(c_ref[:4], 5)}; "
+          f"MSE start {mse_start:.4e}, oracle fit {mse_ref:.4e}, GPU fit {mse_gpu:.4e}; {len(losses) - 1} updates")
+    assert np.max(np.abs(c_gpu - c_ref)) <= 1e-2 * np.max(np.abs(c_ref))
+    assert mse_gpu <= mse_ref * (1 + 1e-5)
+    assert mse_ref < mse_start
+    assert losses[0] == pytest.approx(mse_start, rel=1e-4)
+    assert losses[-1] == pytest.approx(mse_gpu, rel=1e-4)
+    assert all(b <= a * (1 + 1e-9) for a, b in zip(losses, losses[1:]))
+
+
+def test_fit_coeffs_rejects_multi_step_plan_and_keeps_plan_coeffs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_00921_gb300 import DBPError, Plan
+    link = synth.link(10)
+    n = 4096
+    x = (torch.randn(1, 2, n, dtype=torch.complex64, device="cuda") * 0.03).contiguous()
+    with Plan(link, FS, n, method="essfm", n_steps=2, n_taps=4, fft_size=1024) as plan:
+        with pytest.raises(DBPError) as ei:
+            plan.fit_coeffs(x, x)
+        assert ei.value.code == -7
+    with Plan(link, FS, n, method="essfm", n_steps=1, n_taps=4, fft_size=1024) as plan:
+        y0 = plan.run(x)
+        c, losses = plan.fit_coeffs(x, y0 * 1.0001)
+        y1 = plan.run(x)
+        assert torch.equal(y0, y1)
+        with pytest.raises(DBPError) as ei:
+            plan.fit_coeffs(torch.zeros_like(x), y0)
+        assert ei.value.code == -9
