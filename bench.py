@@ -233,6 +233,8 @@ def run_ours(args):
     fp32 = fp32_pipe(value / world, fft_e, pe.info.overlap)
     precision = precision_measure(torch, stream) if not args.no_extras else None
     adjoint = adjoint_measure(torch, stream) if not args.no_extras else None
+    single = single_pol_measure(torch, stream, fft_e) if not args.no_extras else None
+    fit = fit_measure(torch, stream, fft_e) if not args.no_extras else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds, fft_e)
@@ -260,6 +262,8 @@ def run_ours(args):
             "batch": batch,
             "precision_variants": precision,
             "adjoint": adjoint,
+            "single_pol": single,
+            "ls_fit": fit,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -393,6 +397,51 @@ def adjoint_measure(torch, stream):
     out["workload"] = "3200 km ESSFM N_c=16, N=4096, 64 x 2^17 samples, input + coefficient + gamma + dz gradients"
     out["unit"] = UNIT
     return out
+
+
+def single_pol_measure(torch, stream, fft_size: int):
+    """One-polarization ESSFM (N_s = 1, N_c = 32) over 3200 km on 128 waveforms of 2^19
+    samples (512 MiB in, 512 MiB out: larger than L2): scalar samples/s and the HBM
+    fraction at 8 B read + 8 B written per sample."""
+    from paper_1507_00921_gb300 import Plan
+    n, nw = N_SAMPLES, 128
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.BASE_SEED + 5)
+    x = torch.randn((nw, n), dtype=torch.complex64, device="cuda", generator=gen) * math.sqrt(
+        synth.dbm_to_w(2.0))
+    y = torch.empty_like(x)
+    with Plan(synth.link(N_SPANS, manakov_factor=1.0), synth.SAMPLE_RATE, n, n_waveforms=nw, n_pols=1,
+              method="essfm", n_steps=1, n_taps=ESSFM_TAPS, coeffs=essfm_coeffs(ESSFM_TAPS),
+              fft_size=fft_size) as plan:
+        t = time_plan(torch, lambda: plan.run(x, y, stream=stream), stream)
+    rate = nw * n / t
+    peak, peak_kind = hbm_peak()
+    gbs = 16 * rate / 1e9
+    return {"value": round(rate / 1e6, 1), "unit": "Msamples/s (one polarization)", "fft_size": fft_size,
+            "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4), "peak_kind": peak_kind,
+            "workload": f"3200 km scalar link, ESSFM N_s=1 N_c={ESSFM_TAPS}, {nw} x 2^19 samples, one polarization"}
+
+
+def fit_measure(torch, stream, fft_size: int):
+    """Section IV least-squares fit (dbp_fit_coeffs) of a 3200 km single-step ESSFM with
+    N_c = 32 on 8 waveforms of 2^19 samples against a target of the same shape: wall time
+    of the whole fit (Gram matrix, Cholesky, Gauss-Newton passes)."""
+    from paper_1507_00921_gb300 import Plan
+    n, nw = N_SAMPLES, 8
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.BASE_SEED + 6)
+    amp = math.sqrt(synth.dbm_to_w(2.0))
+    x = torch.randn((nw, 2, n), dtype=torch.complex64, device="cuda", generator=gen) * amp
+    t_ = torch.randn((nw, 2, n), dtype=torch.complex64, device="cuda", generator=gen) * amp
+    with Plan(synth.link(N_SPANS), synth.SAMPLE_RATE, n, n_waveforms=nw, method="essfm", n_steps=1,
+              n_taps=ESSFM_TAPS, fft_size=fft_size) as plan:
+        plan.fit_coeffs(x, t_, max_iter=2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, losses = plan.fit_coeffs(x, t_, max_iter=10, tol=0.0)
+        dt = time.perf_counter() - t0
+    return {"seconds": round(dt, 4), "updates": len(losses) - 1, "training_vector_samples": nw * n,
+            "workload": f"3200 km ESSFM N_s=1 N_c={ESSFM_TAPS}, N={fft_size}, {nw} x 2^19 samples, 10 updates"}
 
 
 def fp32_pipe(value_msps: float, fft: int, overlap: int):

@@ -77,6 +77,14 @@ typedef struct {
     int64_t n_samples;          /* samples per polarization per waveform, >= 1           */
     int32_t n_waveforms;        /* independent waveforms in one call, >= 1               */
     int32_t boundary;           /* DBP_PERIODIC or DBP_ZERO                              */
+    int32_t n_pols;             /* 2 (or 0): polarization-multiplexed, complex64 [2][n]
+                                   per waveform, P_k = |y_k,1|^2 + |y_k,2|^2 (Eq. 3);
+                                   1: one polarization, complex64 [n] per waveform, the
+                                   scalar form P_k = |y_k|^2 that Eq. 3 extends (gamma_eff
+                                   uses the link's manakov_factor as given: 1 for a scalar
+                                   link).  n_pols = 1 runs dbp_run, dbp_run_host and both
+                                   schemes at FP32; dbp_grad, dbp_fit_coeffs, the batch calls
+                                   and dbp_run_noalloc return DBP_ERR_UNSUPPORTED for it.  */
 } dbp_signal;
 
 /* The backpropagation steps. */

@@ -44,7 +44,7 @@ class dbp_link(C.Structure):
 
 class dbp_signal(C.Structure):
     _fields_ = [("sample_rate_hz", C.c_double), ("n_samples", C.c_int64), ("n_waveforms", C.c_int32),
-                ("boundary", C.c_int32)]
+                ("boundary", C.c_int32), ("n_pols", C.c_int32)]
 
 
 class dbp_steps(C.Structure):

@@ -110,7 +110,8 @@ extern "C" int dbp_batch_create(dbp_plan_t *const *plans, const void *const *ins
         if (!plans[j] || !ins[j] || !outs[j]) return DBP_ERR_ARG;
         const PlanImpl &P = plans[j]->impl;
         if (P.device != dev) return DBP_ERR_ARG;
-        if (P.precision != DBP_FP32 || P.scheme != DBP_SCHEME_FUSED) return DBP_ERR_UNSUPPORTED;
+        if (P.precision != DBP_FP32 || P.scheme != DBP_SCHEME_FUSED || P.signal.n_pols == 1)
+            return DBP_ERR_UNSUPPORTED;
         const size_t bytes = (size_t)2 * P.signal.n_samples * sizeof(float2) * P.signal.n_waveforms;
         if (overlaps(ins[j], outs[j], bytes)) return DBP_ERR_ALIAS;
     }

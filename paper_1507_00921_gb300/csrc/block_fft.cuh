@@ -149,47 +149,59 @@ struct Blk {
 
     // Block window [win0, win0 + N) of both polarizations of a waveform (pol-major
     // [2][n] complex64) into the pass-1 layout; periodic or zero outside [0, n).
+    // SINGLE: a one-polarization waveform [n], lane l holding the window of the block
+    // `shift` samples later, [win0 + l shift, win0 + l shift + N).
+    template <bool SINGLE = false>
     __device__ __forceinline__ void load_window(Regs &v, const float2 *__restrict__ in, long long n, long long win0,
-                                                int boundary) const {
-        if (win0 >= 0 && win0 + N <= n) {
+                                                int boundary, int shift = 0) const {
+        if (win0 >= 0 && win0 + (SINGLE ? shift : 0) + N <= n) {
 #pragma unroll
-            for (int pol = 0; pol < 2; ++pol)
+            for (int pol = 0; pol < 2; ++pol) {
+                const float2 *base = SINGLE ? in + win0 + (long long)pol * shift : in + pol * n + win0;
 #pragma unroll
                 for (int i = 0; i < C1; ++i)
 #pragma unroll
-                    for (int j = 0; j < N2; ++j) v[pol][i][j] = __ldg(in + pol * n + win0 + pos1(i, j));
+                    for (int j = 0; j < N2; ++j) v[pol][i][j] = __ldg(base + pos1(i, j));
+            }
         } else {
 #pragma unroll
-            for (int pol = 0; pol < 2; ++pol)
+            for (int pol = 0; pol < 2; ++pol) {
+                const float2 *base = SINGLE ? in : in + pol * n;
+                const long long w0 = SINGLE ? win0 + (long long)pol * shift : win0;
 #pragma unroll
                 for (int i = 0; i < C1; ++i)
 #pragma unroll
                     for (int j = 0; j < N2; ++j) {
-                        long long idx = win0 + pos1(i, j);
+                        long long idx = w0 + pos1(i, j);
                         float2 val = make_float2(0.f, 0.f);
                         if (boundary == DBP_PERIODIC) {
                             idx %= n;
                             if (idx < 0) idx += n;
-                            val = __ldg(in + pol * n + idx);
+                            val = __ldg(base + idx);
                         } else if (idx >= 0 && idx < n) {
-                            val = __ldg(in + pol * n + idx);
+                            val = __ldg(base + idx);
                         }
                         v[pol][i][j] = val;
                     }
+            }
         }
     }
 
     // Prefetches a block window's 2 x N complex64 samples into L2 (128-byte lines),
     // clamped to [0, n); a hint only, for the block that will run on this SM next.
-    __device__ __forceinline__ void prefetch_window_l2(const float2 *in, long long n, long long win0) const {
+    // SINGLE: the N + shift samples of a one-polarization block pair.
+    template <bool SINGLE = false>
+    __device__ __forceinline__ void prefetch_window_l2(const float2 *in, long long n, long long win0,
+                                                       int shift = 0) const {
         const long long lo = win0 < 0 ? 0 : win0;
-        const long long hi = win0 + N > n ? n : win0 + N;
+        const long long end = win0 + N + (SINGLE ? shift : 0);
+        const long long hi = end > n ? n : end;
         if (hi <= lo) return;
         const char *base0 = reinterpret_cast<const char *>(in + lo);
         const long long bytes = (hi - lo) * (long long)sizeof(float2);
         for (long long off = (long long)t * 128; off < bytes; off += (long long)T * 128) {
             asm volatile("prefetch.global.L2 [%0];" ::"l"(base0 + off));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(base0 + off + n * (long long)sizeof(float2)));
+            if (!SINGLE) asm volatile("prefetch.global.L2 [%0];" ::"l"(base0 + off + n * (long long)sizeof(float2)));
         }
     }
 
@@ -425,13 +437,25 @@ struct Blk {
 
     // ESSFM phase theta (Eq. 3) of the block in registers, into farr(1).  The block
     // buffer must be free (a barrier after the last pass-1' read); returns after a
-    // barrier, with theta visible to all threads.
+    // barrier, with theta visible to all threads.  LANE < 0: P is the joint intensity of
+    // the two polarizations; LANE = 0 or 1: P = |y|^2 of that lane alone (one-polarization
+    // blocks, the scalar form that Eq. 3 extends).
+    template <int LANE = -1>
     __device__ __forceinline__ void essfm_theta(const Regs &v, const float *a, int n_tapblk) {
         float *sP = farr(0);
 #pragma unroll
         for (int i = 0; i < C1; ++i)
 #pragma unroll
-            for (int j = 0; j < N2; ++j) sP[pphys(pos1(i, j))] = joint_intensity(v[0][i][j], v[1][i][j]);
+            for (int j = 0; j < N2; ++j) {
+                float pk;
+                if constexpr (LANE < 0) {
+                    pk = joint_intensity(v[0][i][j], v[1][i][j]);
+                } else {
+                    const float2 y = v[LANE][i][j];
+                    pk = fmaf(y.x, y.x, y.y * y.y);
+                }
+                sP[pphys(pos1(i, j))] = pk;
+            }
         __syncthreads();
 #ifdef DBP_FIR_TC
         fir_tc(sP, farr(1), a, n_tapblk);

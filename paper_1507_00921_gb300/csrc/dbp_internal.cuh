@@ -69,6 +69,7 @@ struct FwdParams {
     const float2 *tw2;      // [N1][N0] W_{N0 N1}^{n0 k1}
     int prefetch_ahead;     // blocks ahead whose input window is prefetched into L2 (0: off)
     int linear_only;        // 1: skip the nonlinear sub-step (FFE)
+    int single_pol;         // 1: one-polarization waveforms [n], two blocks per CTA
 };
 
 // One job of a batched launch: a plan's parameters with its own input/output buffers.

@@ -196,7 +196,7 @@ extern "C" int dbp_fit_coeffs(dbp_plan_t *plan, const void *x, const void *targe
     if (!plan || !x || !target || !coeffs || max_iter < 0 || !(tol >= 0.0)) return DBP_ERR_ARG;
     PlanImpl &P = plan->impl;
     if (P.method != DBP_ESSFM || P.info.n_steps != 1 || P.precision != DBP_FP32 ||
-        P.scheme != DBP_SCHEME_FUSED)
+        P.scheme != DBP_SCHEME_FUSED || P.signal.n_pols == 1)
         return DBP_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     const int N = P.info.fft_size, V = P.info.valid, half = P.info.overlap / 2;

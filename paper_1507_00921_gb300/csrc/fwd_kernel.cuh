@@ -18,16 +18,18 @@ namespace dbp {
 
 // One overlap-save block (waveform w, block b) of the plan described by p, with the
 // twiddle tables already in shared memory and p.H (step 0) prefetch committed.
-template <int N, bool ESSFM>
+// SINGLE: a one-polarization waveform [n]; the two polarization lanes carry blocks b
+// and b + 1, each with its own intensity P = |y|^2, filter and phase.
+template <int N, bool ESSFM, bool SINGLE = false>
 __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, int w, int b) {
     using B = Blk<N>;
     const long long n = p.n;
-    const float2 *__restrict__ in = p.in + (size_t)w * 2 * n;
-    float2 *__restrict__ out = p.out + (size_t)w * 2 * n;
+    const float2 *__restrict__ in = p.in + (size_t)w * (SINGLE ? 1 : 2) * n;
+    float2 *__restrict__ out = p.out + (size_t)w * (SINGLE ? 1 : 2) * n;
     const long long win0 = (long long)b * p.valid - p.half_overlap;
 
     typename B::Regs v;
-    blk.load_window(v, in, n, win0, p.boundary);
+    blk.template load_window<SINGLE>(v, in, n, win0, p.boundary, p.valid);
 
     MidMulH<N> mid{blk.sH};
     for (int s = 0; s < p.n_steps; ++s) {
@@ -48,7 +50,7 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
 
         // ---- nonlinear sub-step
         const float *__restrict__ a = p.taps + p.taps_stride * s;
-        if constexpr (ESSFM) {
+        if constexpr (ESSFM && !SINGLE) {
             __syncthreads();   // block buffer free: P and theta reuse it
             blk.essfm_theta(v, blk.sa, p.n_tapblk);
             const float *sT = blk.farr(1);
@@ -60,6 +62,32 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
                     v[0][i][j] = cmul(v[0][i][j], e);
                     v[1][i][j] = cmul(v[1][i][j], e);
                 }
+        } else if constexpr (ESSFM) {
+            const float *sT = blk.farr(1);
+            __syncthreads();   // block buffer free
+            blk.template essfm_theta<0>(v, blk.sa, p.n_tapblk);
+#pragma unroll
+            for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+                for (int j = 0; j < B::N2; ++j) v[0][i][j] = cmul(v[0][i][j], expj(sT[pphys(blk.pos1(i, j))]));
+            // lane 1: its P may overwrite lane 0's (the filter is done); the barrier inside
+            // essfm_theta orders the lane-0 theta reads before lane 1's theta is written
+            blk.template essfm_theta<1>(v, blk.sa, p.n_tapblk);
+#pragma unroll
+            for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+                for (int j = 0; j < B::N2; ++j) v[1][i][j] = cmul(v[1][i][j], expj(sT[pphys(blk.pos1(i, j))]));
+        } else if constexpr (SINGLE) {
+            const float a0 = __ldg(a);
+#pragma unroll
+            for (int l = 0; l < 2; ++l)
+#pragma unroll
+                for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+                    for (int j = 0; j < B::N2; ++j) {
+                        const float2 y = v[l][i][j];
+                        v[l][i][j] = cmul(y, expj(a0 * fmaf(y.x, y.x, y.y * y.y)));
+                    }
         } else {
             const float a0 = __ldg(a);
 #pragma unroll
@@ -82,8 +110,12 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
 #pragma unroll
         for (int j = 0; j < B::N2; ++j) {
             const int e = blk.pos1(i, j);
+            if (e < h || e >= h + p.valid) continue;
             const long long g = obase + e;
-            if (e >= h && e < h + p.valid && g < n) {
+            if constexpr (SINGLE) {
+                if (g < n) __stcs(out + g, v[0][i][j]);
+                if (g + p.valid < n) __stcs(out + g + p.valid, v[1][i][j]);
+            } else if (g < n) {
                 __stcs(out + g, v[0][i][j]);
                 __stcs(out + n + g, v[1][i][j]);
             }
@@ -93,23 +125,28 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
 // Persistent over blocks: CTA c processes blocks c, c + gridDim.x, ...  The twiddle
 // tables (and H when all steps share it) are loaded into shared memory once per CTA;
 // the input window of the block this CTA runs next is prefetched into L2 while the
-// current one is processed.
-template <int N, bool ESSFM>
+// current one is processed.  SINGLE: an item is a pair of consecutive blocks of a
+// one-polarization waveform.
+template <int N, bool ESSFM, bool SINGLE = false>
 __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const FwdParams p, int total) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Blk<N> blk(smem_raw, threadIdx.x);
     blk.load_tables(p.twA, p.twB, p.tw2);
+    const int per_wave = SINGLE ? (p.n_blocks + 1) / 2 : p.n_blocks;
+    const int bstep = SINGLE ? 2 : 1;
+    const long long wstride = (SINGLE ? 1 : 2) * p.n;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        const int w = item / p.n_blocks;
-        const int b = item - w * p.n_blocks;
+        const int w = item / per_wave;
+        const int b = (item - w * per_wave) * bstep;
         if (item == (int)blockIdx.x || p.h_stride != 0) blk.prefetch_h(p.H);
         const int next = item + (int)gridDim.x;
         if (p.prefetch_ahead != 0 && next < total) {
-            const int w2 = next / p.n_blocks, b2 = next - w2 * p.n_blocks;
-            blk.prefetch_window_l2(p.in + (size_t)w2 * 2 * p.n, p.n, (long long)b2 * p.valid - p.half_overlap);
+            const int w2 = next / per_wave, b2 = (next - w2 * per_wave) * bstep;
+            blk.template prefetch_window_l2<SINGLE>(p.in + (size_t)w2 * wstride, p.n,
+                                                    (long long)b2 * p.valid - p.half_overlap, p.valid);
         }
         __syncthreads();   // tables visible; previous block's shared-memory use finished
-        process_block<N, ESSFM>(p, blk, w, b);
+        process_block<N, ESSFM, SINGLE>(p, blk, w, b);
         __syncthreads();
     }
 }
@@ -126,29 +163,28 @@ inline int resident_ctas(K kernel, int threads, size_t smem) {
     return r > 0 ? r : 1;
 }
 
-template <int N>
-int launch_fwd_n(const FwdParams &p, int n_wave, bool essfm, cudaStream_t st) {
+template <int N, bool ESSFM, bool SINGLE>
+int launch_fwd_variant(const FwdParams &p, long long grid, cudaStream_t st) {
     using G = Geo<N>;
-    static unsigned long long done_essfm = 0, done_ssfm = 0;
-    const long long grid = (long long)p.n_blocks * n_wave;
-    if (grid <= 0 || grid > 0x7fffffffLL) return DBP_ERR_ARG;
-    static int resident[64][2];   // CTAs resident per GPU (SMs x CTAs per SM), per device and variant
+    static unsigned long long done = 0;
+    static int resident[64];   // CTAs resident per GPU (SMs x CTAs per SM), per device
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DBP_ERR_CUDA;
-    const int v = essfm ? 1 : 0;
-    if (essfm) {
-        if (!set_smem_once(dbp_fwd_kernel<N, true>, G::SMEM, done_essfm)) return DBP_ERR_CUDA;
-        if (!resident[dev][v]) resident[dev][v] = resident_ctas(dbp_fwd_kernel<N, true>, G::T, G::SMEM);
-    } else {
-        if (!set_smem_once(dbp_fwd_kernel<N, false>, G::SMEM, done_ssfm)) return DBP_ERR_CUDA;
-        if (!resident[dev][v]) resident[dev][v] = resident_ctas(dbp_fwd_kernel<N, false>, G::T, G::SMEM);
-    }
-    const int ctas = (int)(grid < resident[dev][v] ? grid : resident[dev][v]);
-    if (essfm)
-        dbp_fwd_kernel<N, true><<<(unsigned)ctas, G::T, G::SMEM, st>>>(p, (int)grid);
-    else
-        dbp_fwd_kernel<N, false><<<(unsigned)ctas, G::T, G::SMEM, st>>>(p, (int)grid);
+    if (!set_smem_once(dbp_fwd_kernel<N, ESSFM, SINGLE>, G::SMEM, done)) return DBP_ERR_CUDA;
+    if (!resident[dev]) resident[dev] = resident_ctas(dbp_fwd_kernel<N, ESSFM, SINGLE>, G::T, G::SMEM);
+    const int ctas = (int)(grid < resident[dev] ? grid : resident[dev]);
+    dbp_fwd_kernel<N, ESSFM, SINGLE><<<(unsigned)ctas, G::T, G::SMEM, st>>>(p, (int)grid);
     return cudaGetLastError() == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
+}
+
+template <int N>
+int launch_fwd_n(const FwdParams &p, int n_wave, bool essfm, cudaStream_t st) {
+    const long long per_wave = p.single_pol ? (p.n_blocks + 1) / 2 : p.n_blocks;
+    const long long grid = per_wave * n_wave;
+    if (grid <= 0 || grid > 0x7fffffffLL) return DBP_ERR_ARG;
+    if (p.single_pol)
+        return essfm ? launch_fwd_variant<N, true, true>(p, grid, st) : launch_fwd_variant<N, false, true>(p, grid, st);
+    return essfm ? launch_fwd_variant<N, true, false>(p, grid, st) : launch_fwd_variant<N, false, false>(p, grid, st);
 }
 
 }  // namespace dbp

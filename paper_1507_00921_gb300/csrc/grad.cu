@@ -126,7 +126,8 @@ extern "C" int dbp_grad(dbp_plan_t *plan, const void *in, const void *grad_out, 
                         float *d_gamma_eff, float *d_step_len, dbp_stream_t stream) {
     if (!plan || !in || !grad_out) return DBP_ERR_ARG;
     PlanImpl &P = plan->impl;
-    if (P.precision != DBP_FP32 || P.scheme != DBP_SCHEME_FUSED) return DBP_ERR_UNSUPPORTED;
+    if (P.precision != DBP_FP32 || P.scheme != DBP_SCHEME_FUSED || P.signal.n_pols == 1)
+        return DBP_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     const int N = P.info.fft_size, ns = P.info.n_steps, nt = P.info.n_taps;
     const int nw = P.signal.n_waveforms;

@@ -47,7 +47,8 @@ extern "C" int dbp_run_noalloc(const dbp_link *link, const dbp_signal *signal, c
     if (!link || !signal || !steps || !in || !out) return DBP_ERR_ARG;
     if (steps->n_steps < 1) return DBP_ERR_ARG;
     if (steps->n_steps > DBP_NOALLOC_MAX_STEPS) return DBP_ERR_SCRATCH;
-    if (steps->precision != DBP_FP32 || steps->scheme != DBP_SCHEME_FUSED) return DBP_ERR_UNSUPPORTED;
+    if (steps->precision != DBP_FP32 || steps->scheme != DBP_SCHEME_FUSED || signal->n_pols == 1)
+        return DBP_ERR_UNSUPPORTED;
     double dz[DBP_NOALLOC_MAX_STEPS], geff[DBP_NOALLOC_MAX_STEPS];
     dbp_plan_info info;
     int rc = describe(link, signal, steps, &info, dz, geff);

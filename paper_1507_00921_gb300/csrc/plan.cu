@@ -105,6 +105,7 @@ static int validate(const dbp_link *link, const dbp_signal *sig, const dbp_steps
         return DBP_ERR_ARG;
     if (!(sig->sample_rate_hz > 0) || sig->n_samples < 1 || sig->n_waveforms < 1) return DBP_ERR_ARG;
     if (sig->boundary != DBP_PERIODIC && sig->boundary != DBP_ZERO) return DBP_ERR_ARG;
+    if (sig->n_pols != 0 && sig->n_pols != 1 && sig->n_pols != 2) return DBP_ERR_ARG;
     if (st->method != DBP_SSFM && st->method != DBP_ESSFM && st->method != DBP_FFE) return DBP_ERR_ARG;
     if (st->scheme != DBP_SCHEME_FUSED && st->scheme != DBP_SCHEME_PER_STEP) return DBP_ERR_ARG;
     if (st->n_steps < 1 || st->n_steps > DBP_MAX_STEPS) return DBP_ERR_ARG;
@@ -119,6 +120,7 @@ static int validate(const dbp_link *link, const dbp_signal *sig, const dbp_steps
         if (N < 1024 || N > 4096 || (NA != 64 && NA != 128 && NA != 256) || N / NA < 4 || N / NA > 32)
             return DBP_ERR_UNSUPPORTED;
     }
+    if (sig->n_pols == 1 && st->precision != DBP_FP32) return DBP_ERR_UNSUPPORTED;
     if (st->overlap < 0 || (st->overlap % 4) != 0) return DBP_ERR_ARG;
     if (st->step_len_m)
         for (int s = 0; s < st->n_steps; ++s)
@@ -296,6 +298,7 @@ static int make_plan(const dbp_link *link, const dbp_signal *sig, const dbp_step
     PlanImpl &P = plan->impl;
     P.link = *link;
     P.signal = *sig;
+    if (P.signal.n_pols == 0) P.signal.n_pols = 2;
     P.info = info;
     P.method = st->method;
     P.coeffs_per_step = st->coeffs_per_step;
@@ -368,6 +371,7 @@ void fill_fwd_params(const PlanImpl &P, FwdParams &p) {
     p.tw2 = P.d_tw2;
     p.prefetch_ahead = P.prefetch_ahead;
     p.linear_only = P.method == DBP_FFE ? 1 : 0;
+    p.single_pol = P.signal.n_pols == 1 ? 1 : 0;
 }
 
 static int launch_fwd(const FwdParams &p, int N, int n_wave, bool essfm, cudaStream_t st) {
@@ -386,7 +390,7 @@ static int launch_fwd(const FwdParams &p, int N, int n_wave, bool essfm, cudaStr
 // `out`.
 static int launch_per_step(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_t st) {
     const int N = P.info.fft_size, ns = P.info.n_steps;
-    const size_t bytes = (size_t)2 * P.signal.n_samples * sizeof(float2) * n_wave;
+    const size_t bytes = (size_t)P.signal.n_pols * P.signal.n_samples * sizeof(float2) * n_wave;
     PlanImpl &M = const_cast<PlanImpl &>(P);
     if (ns > 1 && M.pp_bytes < bytes) {
         if (M.d_pp) cudaFree(M.d_pp);
@@ -441,7 +445,9 @@ int launch(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_
     }
 }
 
-static size_t waveform_bytes(const PlanImpl &P) { return (size_t)2 * P.signal.n_samples * sizeof(float2); }
+static size_t waveform_bytes(const PlanImpl &P) {
+    return (size_t)P.signal.n_pols * P.signal.n_samples * sizeof(float2);
+}
 
 }  // namespace dbp
 

@@ -48,9 +48,10 @@ class _Args:
 
     def __init__(self, link, fs, n_samples, n_waveforms, boundary, method, n_steps, n_taps, coeffs,
                  coeffs_per_step, step_len_m, gamma_eff, fft_size, overlap, precision="fp32", dft_block=0,
-                 scheme="fused"):
+                 scheme="fused", n_pols=2):
         self.link = _link_struct(link)
-        self.signal = _lib.dbp_signal(float(fs), int(n_samples), int(n_waveforms), _BOUNDARY[boundary])
+        self.signal = _lib.dbp_signal(float(fs), int(n_samples), int(n_waveforms), _BOUNDARY[boundary],
+                                      int(n_pols))
         self.coeffs = None if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float32)
         self.step_len = None if step_len_m is None else np.ascontiguousarray(step_len_m, dtype=np.float64)
         self.gamma_eff = None if gamma_eff is None else np.ascontiguousarray(gamma_eff, dtype=np.float64)
@@ -67,11 +68,11 @@ class _Args:
 
 def describe(link: dict, fs: float, n_samples: int, *, n_waveforms=1, boundary="periodic", method="essfm",
              n_steps=1, n_taps=0, coeffs=None, coeffs_per_step=False, step_len_m=None, gamma_eff=None,
-             fft_size=4096, overlap=0, precision="fp32", dft_block=0, scheme="fused") -> PlanInfo:
+             fft_size=4096, overlap=0, precision="fp32", dft_block=0, scheme="fused", n_pols=2) -> PlanInfo:
     """Plan geometry and step table, computed by libdbp on the host (no GPU needed)."""
     lib = _lib.load()
     a = _Args(link, fs, n_samples, n_waveforms, boundary, method, n_steps, n_taps, coeffs, coeffs_per_step,
-              step_len_m, gamma_eff, fft_size, overlap, precision, dft_block, scheme)
+              step_len_m, gamma_eff, fft_size, overlap, precision, dft_block, scheme, n_pols)
     info = _lib.dbp_plan_info()
     dz = np.zeros(n_steps)
     ge = np.zeros(n_steps)
@@ -88,21 +89,25 @@ class Plan:
 
     def __init__(self, link: dict, fs: float, n_samples: int, *, n_waveforms=1, boundary="periodic",
                  method="essfm", n_steps=1, n_taps=0, coeffs=None, coeffs_per_step=False, step_len_m=None,
-                 gamma_eff=None, fft_size=4096, overlap=0, precision="fp32", dft_block=0, scheme="fused"):
+                 gamma_eff=None, fft_size=4096, overlap=0, precision="fp32", dft_block=0, scheme="fused",
+                 n_pols=2):
+        """``n_pols=1``: one-polarization waveforms, complex64 [n_waveforms, n] (or
+        [n_waveforms, 1, n]), the scalar ESSFM / SSFM with P_k = |y_k|^2."""
         import torch
         self._lib = _lib.load()
         self._args = _Args(link, fs, n_samples, n_waveforms, boundary, method, n_steps, n_taps, coeffs,
                            coeffs_per_step, step_len_m, gamma_eff, fft_size, overlap, precision, dft_block,
-                           scheme)
+                           scheme, n_pols)
         self.n_samples = int(n_samples)
         self.n_waveforms = int(n_waveforms)
+        self.n_pols = int(n_pols) if n_pols else 2
         self.method = method
         self.coeffs_per_step = bool(coeffs_per_step)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.info = describe(link, fs, n_samples, n_waveforms=n_waveforms, boundary=boundary, method=method,
                              n_steps=n_steps, n_taps=n_taps, coeffs=coeffs, coeffs_per_step=coeffs_per_step,
                              step_len_m=step_len_m, gamma_eff=gamma_eff, fft_size=fft_size, overlap=overlap,
-                             precision=precision, dft_block=dft_block, scheme=scheme)
+                             precision=precision, dft_block=dft_block, scheme=scheme, n_pols=n_pols)
         h = C.c_void_p()
         rc = self._lib.dbp_plan(C.byref(self._args.link), C.byref(self._args.signal), C.byref(self._args.steps),
                                 C.byref(h))
@@ -116,9 +121,13 @@ class Plan:
             raise TypeError(f"{name} must be a CUDA complex64 tensor")
         if x.device != self.device:
             raise ValueError(f"{name} is on {x.device}, plan on {self.device}")
-        want = (self.n_waveforms, 2, self.n_samples)
-        if x.numel() != np.prod(want) or x.shape[-2:] != (2, self.n_samples):
-            raise ValueError(f"{name} must have shape {want} (or [2, n] for one waveform)")
+        want = (self.n_waveforms, self.n_pols, self.n_samples)
+        if self.n_pols == 1:
+            ok = x.numel() == np.prod(want) and x.shape[-1] == self.n_samples
+        else:
+            ok = x.numel() == np.prod(want) and x.shape[-2:] == (2, self.n_samples)
+        if not ok:
+            raise ValueError(f"{name} must have shape {want} (or [{self.n_pols}, n] for one waveform)")
         if not x.is_contiguous():
             raise ValueError(f"{name} must be contiguous")
 
@@ -142,7 +151,7 @@ class Plan:
         xt = torch.as_tensor(x)
         if xt.is_cuda or xt.dtype != torch.complex64 or not xt.is_contiguous():
             raise TypeError("x must be a contiguous host complex64 array")
-        if xt.numel() != self.n_waveforms * 2 * self.n_samples:
+        if xt.numel() != self.n_waveforms * self.n_pols * self.n_samples:
             raise ValueError("x has the wrong number of samples")
         if out is None:
             out = torch.empty(xt.shape, dtype=torch.complex64, pin_memory=xt.is_pinned())

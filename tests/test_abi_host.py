@@ -75,6 +75,8 @@ def test_plan_nonuniform_steps_and_overrides():
     (dict(n_steps=0), _lib.DBP_ERR_ARG),
     (dict(n_samples=0), _lib.DBP_ERR_ARG),
     (dict(n_waveforms=0), _lib.DBP_ERR_ARG),
+    (dict(n_pols=3), _lib.DBP_ERR_ARG),
+    (dict(n_pols=1, precision="split_bf16", dft_block=128, fft_size=2048), _lib.DBP_ERR_UNSUPPORTED),
 ])
 def test_invalid_arguments_rejected(kw, code):
     kw = dict(kw)
@@ -100,9 +102,10 @@ def test_null_arguments_and_strerror():
     assert lib.dbp_batch_run(None, None) == _lib.DBP_ERR_ARG
     assert lib.dbp_batch_publish(None, 0, None) == _lib.DBP_ERR_ARG
     assert lib.dbp_batch_status(None) == _lib.DBP_ERR_ARG
+    assert lib.dbp_fit_coeffs(None, None, None, 0, 10, 0.0, None, None, None, None) == _lib.DBP_ERR_ARG
     lib.dbp_batch_destroy(None)
     lib.dbp_destroy(None)
-    for code in range(-7, 1):
+    for code in range(-9, 1):
         assert lib.dbp_strerror(code) not in (b"", b"unknown error")
     assert lib.dbp_strerror(-99) == b"unknown error"
     info = _lib.dbp_plan_info()

@@ -153,6 +153,32 @@ def test_link_exact_inverse_recovers_tx():
     assert rel(back, tx) < 1e-11
 
 
+
+def test_single_polarization_scalar_case():
+    """One polarization (the scalar form Eq. 3 extends, P_k = |y_k|^2): (i) a CW field is
+    untouched by dispersion (H(0) = 1), so every step rotates it by gamma_eff_s (c_0 +
+    2 sum_i c_i) |A|^2 -- closed form for the whole DBP; (ii) on [1, n] the oracle equals
+    the dual-polarization oracle with the second polarization zero; (iii) the scalar link
+    (manakov factor 1) is inverted exactly."""
+    link = synth.link(4, manakov_factor=1.0)
+    n, amp = 4096, 0.07
+    cw = np.full((1, n), amp * np.exp(0.3j))
+    c = np.array([0.5, 0.2, 0.05, 0.01])
+    cfg = fiber.make_config(link, FS, 3, 3, 1024, coeffs=c)
+    phase = np.sum(cfg.gamma_eff) * (c[0] + 2 * c[1:].sum()) * amp ** 2
+    np.testing.assert_allclose(dbp.dbp(cw, cfg), cw * np.exp(1j * phase), rtol=0, atol=1e-12)
+
+    tx, _, _ = synth.pm_qpsk_waveform(2 ** 11, 31, 2.0)
+    r1 = olink.forward(tx[:1], link, FS, steps_per_span=20)
+    r2 = np.concatenate([r1, np.zeros_like(r1)], axis=0)
+    for method_cfg in (fiber.make_config(link, FS, 1, 8, 1024), fiber.make_config(link, FS, 5, 0, 1024)):
+        z1 = dbp.dbp(r1, method_cfg)
+        z2 = dbp.dbp(r2, method_cfg)
+        np.testing.assert_array_equal(z1[0], z2[0])
+        assert not np.any(z2[1])
+    assert rel(r1, tx[:1]) > 0.5
+    assert rel(olink.inverse(r1, link, FS, steps_per_span=20), tx[:1]) < 1e-11
+
 def test_ssfm_dbp_error_falls_with_steps():
     link = synth.link(10)
     tx, _, _ = synth.pm_qpsk_waveform(2 ** 11, 10, 2.0)
