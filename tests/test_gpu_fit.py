@@ -108,3 +108,32 @@ def test_fit_coeffs_rejects_multi_step_plan_and_keeps_plan_coeffs():
         with pytest.raises(DBPError) as ei:
             plan.fit_coeffs(torch.zeros_like(x), y0)
         assert ei.value.code == -9
+
+
+def test_gauss_newton_fit_on_gpu_recovers_known_coefficients():
+    """Section IV fit, noise-free: the target is the FP64 oracle's single-step ESSFM output
+    with known coefficients c_true on the same block geometry, so the minimum-MSE fit
+    through dbp_fit_coeffs must return c_true (to the FP32 precision of the GPU's linear
+    sub-step), starting from the SSFM, and the final loss must be near zero."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import dbp as odbp
+    from oracle import fiber
+    from paper_1507_00921_gb300.fit import fit_gauss_newton
+    link = synth.link(10)
+    nc, fft = 6, 1024
+    tx, _, _ = synth.pm_qpsk_waveform(2 ** 12, synth.BASE_SEED + 995, 2.0)
+    r = olink.forward(tx, link, FS, steps_per_span=20, ase_seed=synth.BASE_SEED + 996)
+    r32 = r.astype(np.complex64)
+    c_true = np.array([0.31, 0.2, 0.12, 0.07, 0.04, 0.02, 0.01])
+    cfg = fiber.make_config(link, FS, 1, nc, fft, coeffs=c_true)
+    target = odbp.dbp(r32.astype(np.complex128), cfg)
+    c_gpu, losses = fit_gauss_newton(link, FS, torch.from_numpy(r32).cuda(),
+                                     torch.from_numpy(target.astype(np.complex64)).cuda(), nc, fft)
+    energy = float(np.mean(np.sum(np.abs(target) ** 2, axis=0)))
+    print(f"\nrecovered {np.round(c_gpu, 6)} (true {c_true}); loss {losses[0]:.3e} -> {losses[-1]:.3e}, "
+          f"signal {energy:.3e}")
+    assert np.max(np.abs(c_gpu - c_true)) <= 1e-4
+    assert losses[-1] <= 1e-7 * energy
+    assert losses[-1] < 1e-3 * losses[0]
