@@ -31,6 +31,22 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Bulk (TMA-unit) copies: shared -> global stores tracked per issuing thread with bulk
+// groups, and L2 prefetches of a contiguous global range.  Addresses 16-byte aligned,
+// sizes multiples of 16 bytes.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, unsigned bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(ssrc);
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst), "r"(s), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_prefetch_l2(const void *g, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(g), "r"(bytes) : "memory");
+}
+
 // exp(+j theta) for the nonlinear rotation.
 // Default: theta = q pi/2 + r with a three-constant Cody-Waite reduction (pi/2 =
 // 1.5703125 + 4.837512969970703e-4 + 7.549790126404332e-8; the first two constants have
@@ -187,21 +203,40 @@ struct Blk {
         }
     }
 
-    // Prefetches a block window's 2 x N complex64 samples into L2 (128-byte lines),
-    // clamped to [0, n); a hint only, for the block that will run on this SM next.
-    // SINGLE: the N + shift samples of a one-polarization block pair.
-    template <bool SINGLE = false>
+    // Prefetches a block window's 2 x N complex64 samples into L2, clamped to [0, n); a
+    // hint only, for the block that will run on this SM next.  SINGLE: the N + shift
+    // samples of a one-polarization block pair.
+    // BULK: bulk prefetches of 16 KB pieces, one per thread among the first threads of
+    // the CTA, each trimmed inward to 16-byte boundaries; otherwise one 128-byte line per
+    // thread and instruction.
+    template <bool SINGLE = false, bool BULK = false>
     __device__ __forceinline__ void prefetch_window_l2(const float2 *in, long long n, long long win0,
                                                        int shift = 0) const {
         const long long lo = win0 < 0 ? 0 : win0;
         const long long end = win0 + N + (SINGLE ? shift : 0);
         const long long hi = end > n ? n : end;
-        if (hi <= lo) return;
-        const char *base0 = reinterpret_cast<const char *>(in + lo);
-        const long long bytes = (hi - lo) * (long long)sizeof(float2);
-        for (long long off = (long long)t * 128; off < bytes; off += (long long)T * 128) {
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(base0 + off));
-            if (!SINGLE) asm volatile("prefetch.global.L2 [%0];" ::"l"(base0 + off + n * (long long)sizeof(float2)));
+        if constexpr (BULK) {
+            constexpr int CHUNK = 16384;
+            constexpr int CH = (int)(((SINGLE ? 2 : 1) * (long long)N * 8 + CHUNK - 1) / CHUNK);   // pieces per row
+            constexpr int NPOL = SINGLE ? 1 : 2;
+            if (t >= NPOL * CH) return;
+            const int pol = t / CH, c = t - pol * CH;
+            const char *row = reinterpret_cast<const char *>(in + pol * n);
+            unsigned long long a = reinterpret_cast<unsigned long long>(row + lo * 8) + (unsigned long long)c * CHUNK;
+            unsigned long long z = reinterpret_cast<unsigned long long>(row + hi * 8);
+            if (a + CHUNK < z) z = a + CHUNK;
+            a = (a + 15) & ~15ull;
+            z &= ~15ull;
+            if (hi > lo && z > a) bulk_prefetch_l2(reinterpret_cast<const void *>(a), (unsigned)(z - a));
+        } else {
+            if (hi <= lo) return;
+            const char *base0 = reinterpret_cast<const char *>(in + lo);
+            const long long bytes = (hi - lo) * (long long)sizeof(float2);
+            for (long long off = (long long)t * 128; off < bytes; off += (long long)T * 128) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(base0 + off));
+                if (!SINGLE)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(base0 + off + n * (long long)sizeof(float2)));
+            }
         }
     }
 

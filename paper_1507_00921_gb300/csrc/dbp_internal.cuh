@@ -70,6 +70,8 @@ struct FwdParams {
     int prefetch_ahead;     // blocks ahead whose input window is prefetched into L2 (0: off)
     int linear_only;        // 1: skip the nonlinear sub-step (FFE)
     int single_pol;         // 1: one-polarization waveforms [n], two blocks per CTA
+    int bulk_store;         // 1: outputs staged in shared memory, written by bulk copies
+                            //    (out 16-byte aligned and n even; ESSFM kernels)
 };
 
 // One job of a batched launch: a plan's parameters with its own input/output buffers.

@@ -30,6 +30,10 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
 
     typename B::Regs v;
     blk.template load_window<SINGLE>(v, in, n, win0, p.boundary, p.valid);
+    if (ESSFM && p.bulk_store) {   // the previous block's output copy must have read shared memory
+        if (threadIdx.x == 0) bulk_wait_read_all();
+        __syncthreads();
+    }
 
     MidMulH<N> mid{blk.sH};
     for (int s = 0; s < p.n_steps; ++s) {
@@ -105,6 +109,35 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
     // ---- overlap-and-save: keep the central V samples
     const int h = p.half_overlap;
     const long long obase = (long long)b * p.valid - h;
+    if (ESSFM && p.bulk_store) {
+        // stage [2][V] (polarizations, or the two blocks of a one-polarization pair) in
+        // the block buffer, then one thread copies each half to its place in `out`
+        const int V = p.valid;
+        float2 *stage = reinterpret_cast<float2 *>(blk.xs);
+        __syncthreads();   // all reads of P / theta / the block buffer are done
+#pragma unroll
+        for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+            for (int j = 0; j < B::N2; ++j) {
+                const int e = blk.pos1(i, j);
+                if (e < h || e >= h + V) continue;
+                stage[e - h] = v[0][i][j];
+                stage[V + e - h] = v[1][i][j];
+            }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                const long long g0 = (long long)(b + (SINGLE ? l : 0)) * V;
+                const long long cnt = n - g0 < V ? n - g0 : V;
+                if (cnt > 0)
+                    bulk_store(out + (SINGLE ? 0 : l * n) + g0, stage + l * V, (unsigned)(cnt * sizeof(float2)));
+            }
+            bulk_commit();
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < B::C1; ++i)
 #pragma unroll
@@ -142,13 +175,14 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
         const int next = item + (int)gridDim.x;
         if (p.prefetch_ahead != 0 && next < total) {
             const int w2 = next / per_wave, b2 = (next - w2 * per_wave) * bstep;
-            blk.template prefetch_window_l2<SINGLE>(p.in + (size_t)w2 * wstride, p.n,
+            blk.template prefetch_window_l2<SINGLE, ESSFM>(p.in + (size_t)w2 * wstride, p.n,
                                                     (long long)b2 * p.valid - p.half_overlap, p.valid);
         }
         __syncthreads();   // tables visible; previous block's shared-memory use finished
         process_block<N, ESSFM, SINGLE>(p, blk, w, b);
         __syncthreads();
     }
+    if (ESSFM && p.bulk_store && threadIdx.x == 0) bulk_wait_all();
 }
 
 // SMs x resident CTAs per SM for a kernel configuration (at least 1).

@@ -372,6 +372,13 @@ void fill_fwd_params(const PlanImpl &P, FwdParams &p) {
     p.prefetch_ahead = P.prefetch_ahead;
     p.linear_only = P.method == DBP_FFE ? 1 : 0;
     p.single_pol = P.signal.n_pols == 1 ? 1 : 0;
+    p.bulk_store = 0;
+}
+
+// Outputs can be written by bulk copies when every waveform's polarization rows start
+// on 16-byte boundaries.
+static int bulk_ok(const void *out, long long n) {
+    return ((uintptr_t)out % 16 == 0 && n % 2 == 0) ? 1 : 0;
 }
 
 static int launch_fwd(const FwdParams &p, int N, int n_wave, bool essfm, cudaStream_t st) {
@@ -413,6 +420,7 @@ static int launch_per_step(const PlanImpl &P, const void *in, void *out, int n_w
         }
         p.in = (const float2 *)src;
         p.out = (float2 *)dst;
+        p.bulk_store = bulk_ok(dst, P.signal.n_samples);
         p.n_steps = 1;
         p.valid = N - o;
         p.half_overlap = o / 2;
@@ -434,6 +442,7 @@ int launch(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_
     fill_fwd_params(P, p);
     p.in = (const float2 *)in;
     p.out = (float2 *)out;
+    p.bulk_store = bulk_ok(out, P.signal.n_samples);
     const bool essfm = P.method == DBP_ESSFM;
     switch (P.info.fft_size) {
         case 512: return launch_fwd_512(p, n_wave, essfm, st);
