@@ -16,24 +16,28 @@
 
 namespace dbp {
 
-// One overlap-save block (waveform w, block b) of the plan described by p, with the
-// twiddle tables already in shared memory and p.H (step 0) prefetch committed.
-// SINGLE: a one-polarization waveform [n]; the two polarization lanes carry blocks b
-// and b + 1, each with its own intensity P = |y|^2, filter and phase.
-template <int N, bool ESSFM, bool SINGLE = false>
-__device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, int w, int b) {
-    using B = Blk<N>;
+// Input window of overlap-save block (waveform w, block b) into registers (global
+// loads only, no shared memory).  SINGLE: a one-polarization waveform [n]; the two
+// polarization lanes carry blocks b and b + 1.
+template <int N, bool SINGLE = false>
+__device__ __forceinline__ void load_block(const FwdParams &p, const Blk<N> &blk, int w, int b,
+                                           typename Blk<N>::Regs &v) {
     const long long n = p.n;
     const float2 *__restrict__ in = p.in + (size_t)w * (SINGLE ? 1 : 2) * n;
-    float2 *__restrict__ out = p.out + (size_t)w * (SINGLE ? 1 : 2) * n;
-    const long long win0 = (long long)b * p.valid - p.half_overlap;
+    blk.template load_window<SINGLE>(v, in, n, (long long)b * p.valid - p.half_overlap, p.boundary, p.valid);
+}
 
-    typename B::Regs v;
-    blk.template load_window<SINGLE>(v, in, n, win0, p.boundary, p.valid);
-    if (ESSFM && p.bulk_store) {   // the previous block's output copy must have read shared memory
-        if (threadIdx.x == 0) bulk_wait_read_all();
-        __syncthreads();
-    }
+// All steps and the overlap-save output of block (w, b), loaded into v, with the
+// twiddle tables in shared memory, p.H (step 0) prefetch committed and a barrier since
+// the previous block's last shared-memory access (and, with bulk stores, since its
+// output copy finished reading the staging buffer).  SINGLE: each lane has its own
+// intensity P = |y|^2, filter and phase.
+template <int N, bool ESSFM, bool SINGLE = false>
+__device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, int w, int b,
+                                              typename Blk<N>::Regs &v) {
+    using B = Blk<N>;
+    const long long n = p.n;
+    float2 *__restrict__ out = p.out + (size_t)w * (SINGLE ? 1 : 2) * n;
 
     MidMulH<N> mid{blk.sH};
     for (int s = 0; s < p.n_steps; ++s) {
@@ -155,10 +159,23 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
         }
 }
 
+// One block from load to output (batched launches): load, then compute.
+template <int N, bool ESSFM, bool SINGLE = false>
+__device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, int w, int b) {
+    typename Blk<N>::Regs v;
+    load_block<N, SINGLE>(p, blk, w, b, v);
+    if (ESSFM && p.bulk_store) {   // the previous block's output copy must have read shared memory
+        if (threadIdx.x == 0) bulk_wait_read_all();
+        __syncthreads();
+    }
+    compute_block<N, ESSFM, SINGLE>(p, blk, w, b, v);
+}
+
 // Persistent over blocks: CTA c processes blocks c, c + gridDim.x, ...  The twiddle
 // tables (and H when all steps share it) are loaded into shared memory once per CTA;
 // the input window of the block this CTA runs next is prefetched into L2 while the
-// current one is processed.  SINGLE: an item is a pair of consecutive blocks of a
+// current one is processed.  One barrier per block boundary: the steps' own barriers
+// already separate the last reads of H and of the taps from the next block's writes.  SINGLE: an item is a pair of consecutive blocks of a
 // one-polarization waveform.
 template <int N, bool ESSFM, bool SINGLE = false>
 __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const FwdParams p, int total) {
@@ -178,9 +195,14 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
             blk.template prefetch_window_l2<SINGLE, ESSFM>(p.in + (size_t)w2 * wstride, p.n,
                                                     (long long)b2 * p.valid - p.half_overlap, p.valid);
         }
+        // The loads go out before the barrier: they touch registers only.  The barrier then
+        // orders every shared-memory access of the previous block (the last ones: theta reads
+        // or the output staging, whose bulk copy thread 0 waits for) before this block's.
+        typename Blk<N>::Regs v;
+        load_block<N, SINGLE>(p, blk, w, b, v);
+        if (ESSFM && p.bulk_store && threadIdx.x == 0) bulk_wait_read_all();
         __syncthreads();   // tables visible; previous block's shared-memory use finished
-        process_block<N, ESSFM, SINGLE>(p, blk, w, b);
-        __syncthreads();
+        compute_block<N, ESSFM, SINGLE>(p, blk, w, b, v);
     }
     if (ESSFM && p.bulk_store && threadIdx.x == 0) bulk_wait_all();
 }
