@@ -517,6 +517,55 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """The 3200 km sweep of the scope table's configuration 2 (one GPU): SSFM with
+    N_s in {1, 2, 5, 10, 20, 40} and ESSFM with N_s in {1, 2, 4}, N_c in {1, 4, 8, 16, 32},
+    over block lengths N in {512, ..., 8192}, fused scheme, then the per-step-pass scheme
+    for the N that cannot hold the full-link overlap.  Throughput in vector samples/s on
+    64 waveforms of 2^19 samples (256 MiB in, 256 MiB out: larger than L2), CUDA events,
+    and the HBM fraction at 32 B per vector sample.  Infeasible points are reported as
+    such.  One JSON line per point, then one summary line."""
+    import torch
+
+    from paper_1507_00921_gb300 import DBPError, Plan
+    torch.cuda.set_device(0)
+    nw = 64
+    x = torch.from_numpy(synth.received_like(nw, N_SYMBOLS, LAUNCH_DBM, seed=synth.BASE_SEED + 7, distinct=4)).cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.Stream()
+    peak, peak_kind = hbm_peak()
+    link = synth.link(N_SPANS)
+    points = [("ssfm", ns, 0) for ns in (1, 2, 5, 10, 20, 40)]
+    points += [("essfm", ns, nc) for ns in (1, 2, 4) for nc in (1, 4, 8, 16, 32)]
+    best = {}
+    for method, ns, nc in points:
+        for scheme in (("fused",) if ns == 1 else ("fused", "per_step")):
+            for fft in (512, 1024, 2048, 4096, 8192):
+                kw = dict(n_waveforms=nw, method=method, n_steps=ns, n_taps=nc, fft_size=fft, scheme=scheme)
+                if method == "essfm":
+                    kw["coeffs"] = essfm_coeffs(nc)
+                rec = {"method": method, "n_steps": ns, "n_taps": nc, "fft_size": fft, "scheme": scheme}
+                try:
+                    plan = Plan(link, synth.SAMPLE_RATE, N_SAMPLES, **kw)
+                except DBPError as e:
+                    rec["infeasible"] = str(e)
+                    print(json.dumps(rec), flush=True)
+                    continue
+                reps = 5 if method == "essfm" or ns <= 5 else 2
+                t = time_plan(torch, lambda: plan.run(x, y, stream=stream), stream, reps=reps)
+                plan.close()
+                rate = nw * N_SAMPLES / t
+                rec.update(value=round(rate / 1e6, 1), unit=UNIT, hbm_frac=round(BYTES_PER_VSAMPLE * rate / 1e9 / peak, 4))
+                print(json.dumps(rec), flush=True)
+                key = (method, ns, nc)
+                if key not in best or rec["value"] > best[key]["value"]:
+                    best[key] = rec
+    summary = [{"method": k[0], "n_steps": k[1], "n_taps": k[2], "best_fft_size": v["fft_size"],
+                "scheme": v["scheme"], "value": v["value"], "hbm_frac": v["hbm_frac"]} for k, v in best.items()]
+    print(json.dumps({"sweep": "3200 km, 64 x 2^19 vector samples per launch", "unit": UNIT,
+                      "peak_gbs": peak, "peak_kind": peak_kind, "best": summary}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -529,11 +578,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-jobs", type=int, default=256, help="uneven batched workload size (0: skip)")
     ap.add_argument("--no-extras", action="store_true", help="skip the precision-variant and adjoint lines")
+    ap.add_argument("--sweep", action="store_true", help="3200 km method / steps / taps / block-length sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 
