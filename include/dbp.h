@@ -38,7 +38,7 @@ extern "C" {
 #define DBP_ERR_CUDA        -4   /* a CUDA runtime call failed                        */
 #define DBP_ERR_TIMEOUT     -5   /* a bounded device wait gave up (batched launch)    */
 #define DBP_ERR_ALIAS       -6   /* output buffer overlaps the input buffer           */
-#define DBP_ERR_UNSUPPORTED -7   /* option not available in this build                */
+#define DBP_ERR_UNSUPPORTED -7   /* option not supported for this plan or call         */
 #define DBP_ERR_SCRATCH     -8   /* dbp_run_noalloc: problem exceeds its fixed scratch */
 #define DBP_ERR_SINGULAR    -9   /* dbp_fit_coeffs: normal equations not positive definite */
 

@@ -10,7 +10,7 @@ for each block of N vector samples (both polarizations), for each step s:
   (iv)  z_k = y_k exp(+j theta_k)                         (Eq. 2 or Eq. 3, inverted)
 then keep the central N - O samples of each block.
 
-Readings (also in the design doc): backpropagation inverts the paper's forward operators,
+Readings of the paper: backpropagation inverts the paper's forward operators,
 i.e. H_s = exp(+j 2 pi^2 beta2 f^2 dz_s) and a +j nonlinear phase; the order inside a
 step stays the paper's (linear, then nonlinear); the ESSFM filter indices k-i, k+i are
 circular inside the block (the wrapped values land in the discarded overlap).

@@ -1,6 +1,6 @@
 """Fibre parameters, effective lengths, step table and overlap rule (oracle, float64).
 
-Readings of the paper used here (each also listed in the design doc):
+Readings of the paper used here:
 
 * beta2 = -D lambda^2 / (2 pi c); the paper quotes |beta2| = 21 ps^2/km (Section III,
   Fig. 2 discussion) and D is given in ps/(nm km).  lambda is not given: 1550 nm.

@@ -3,7 +3,7 @@ data-aided gain, Gray QPSK decisions, BER and Q-factor.
 
 Stands in for the offline chain of Section IV (resampling, butterfly equaliser,
 asynchronous detection, decisions), which corrects impairments the synthetic link
-does not have (PMD, laser phase noise, frequency offset).  Readings (DESIGN.md):
+does not have (PMD, laser phase noise, frequency offset).  Readings:
 one least-squares complex gain per polarization against the transmitted symbols;
 Q_dB = 10 log10(SNR_eff) with SNR_eff = E|s|^2 / E|s_hat - s|^2 (for Gray QPSK in
 Gaussian noise BER = erfc(Q / sqrt 2) / 2 with Q^2 = SNR); decisions take the sign
