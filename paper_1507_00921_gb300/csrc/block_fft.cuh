@@ -48,43 +48,48 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *g, unsigned bytes) 
 }
 
 // exp(+j theta) for the nonlinear rotation.
-// Default: theta = q pi/2 + r with a three-constant Cody-Waite reduction (pi/2 =
-// 1.5703125 + 4.837512969970703e-4 + 7.549790126404332e-8; the first two constants have
-// 12 significant bits, so q times each is exact for |q| < 2^12, i.e. |theta| < 6400 rad),
-// then Taylor polynomials of sin and cos on |r| <= pi/4 (truncation below 2e-9, under
-// half an FP32 ulp), and the quadrant q mod 4 selects/negates.  With DBP_EXPJ_MUFU the
-// reduction is by 2 pi and the hardware sine/cosine approximations are used instead
-// (absolute error below 4e-7 on [-pi, pi]).
+// Accurate (default): theta = q pi/2 + r with a three-constant Cody-Waite reduction
+// (pi/2 = 1.5703125 + 4.837512969970703e-4 + 7.549790126404332e-8; the first two
+// constants have 12 significant bits, so q times each is exact for |q| < 2^12, i.e.
+// |theta| < 6400 rad), then Taylor polynomials of sin and cos on |r| <= pi/4
+// (truncation below 2e-9, under half an FP32 ulp), and the quadrant q mod 4
+// selects/negates.  Absolute error about 7e-8.
+// FAST: reduction by 2 pi (6.28125 + 1.9353071795864769e-3, the first with 9
+// significant bits) to [-pi, pi] and the hardware sine/cosine approximations, absolute
+// error below 4e-7 there.  The error adds up over the steps of a plan, so the forward
+// kernels take it only for plans of at most two steps (at most 8e-7 of phase, against
+// a parity bar of 1e-5 relative).
+template <bool FAST = false>
 __device__ __forceinline__ float2 expj(float th) {
-#ifdef DBP_EXPJ_MUFU
-    const float k = rintf(th * 0.15915494309189535f);
-    float r = fmaf(-k, 6.28125f, th);
-    r = fmaf(-k, 1.9353071795864769e-3f, r);
-    float s, c;
-    __sincosf(r, &s, &c);
-    return make_float2(c, s);
-#else
-    const float q = rintf(th * 0.63661977236758134f);
-    float r = fmaf(-q, 1.5703125f, th);
-    r = fmaf(-q, 4.837512969970703e-4f, r);
-    r = fmaf(-q, 7.549790126404332e-8f, r);
-    const float r2 = r * r;
-    // sin r = r - r^3/3! + r^5/5! - r^7/7! + r^9/9!
-    float ps = fmaf(r2, 2.7557319223985893e-6f, -1.9841269841269841e-4f);
-    ps = fmaf(r2, ps, 8.3333333333333333e-3f);
-    ps = fmaf(r2, ps, -1.6666666666666667e-1f);
-    const float sn = fmaf(r * r2, ps, r);
-    // cos r = 1 - r^2/2! + r^4/4! - r^6/6! + r^8/8! - r^10/10!
-    float pc = fmaf(r2, -2.7557319223985891e-7f, 2.4801587301587302e-5f);
-    pc = fmaf(r2, pc, -1.3888888888888889e-3f);
-    pc = fmaf(r2, pc, 4.1666666666666667e-2f);
-    pc = fmaf(r2, pc, -0.5f);
-    const float cs = fmaf(r2, pc, 1.0f);
-    const int quad = ((int)q) & 3;
-    const float c1 = (quad & 1) ? sn : cs;
-    const float s1 = (quad & 1) ? cs : sn;
-    return make_float2((quad == 1 || quad == 2) ? -c1 : c1, (quad >= 2) ? -s1 : s1);
-#endif
+    if constexpr (FAST) {
+        const float k = rintf(th * 0.15915494309189535f);
+        float r = fmaf(-k, 6.28125f, th);
+        r = fmaf(-k, 1.9353071795864769e-3f, r);
+        float s, c;
+        __sincosf(r, &s, &c);
+        return make_float2(c, s);
+    } else {
+        const float q = rintf(th * 0.63661977236758134f);
+        float r = fmaf(-q, 1.5703125f, th);
+        r = fmaf(-q, 4.837512969970703e-4f, r);
+        r = fmaf(-q, 7.549790126404332e-8f, r);
+        const float r2 = r * r;
+        // sin r = r - r^3/3! + r^5/5! - r^7/7! + r^9/9!
+        float ps = fmaf(r2, 2.7557319223985893e-6f, -1.9841269841269841e-4f);
+        ps = fmaf(r2, ps, 8.3333333333333333e-3f);
+        ps = fmaf(r2, ps, -1.6666666666666667e-1f);
+        const float sn = fmaf(r * r2, ps, r);
+        // cos r = 1 - r^2/2! + r^4/4! - r^6/6! + r^8/8! - r^10/10!
+        float pc = fmaf(r2, -2.7557319223985891e-7f, 2.4801587301587302e-5f);
+        pc = fmaf(r2, pc, -1.3888888888888889e-3f);
+        pc = fmaf(r2, pc, 4.1666666666666667e-2f);
+        pc = fmaf(r2, pc, -0.5f);
+        const float cs = fmaf(r2, pc, 1.0f);
+        const int quad = ((int)q) & 3;
+        const float c1 = (quad & 1) ? sn : cs;
+        const float s1 = (quad & 1) ? cs : sn;
+        return make_float2((quad == 1 || quad == 2) ? -c1 : c1, (quad >= 2) ? -s1 : s1);
+    }
 }
 
 // TF32 helpers for the tensor-core filter: x = hi + lo with both parts TF32-rounded

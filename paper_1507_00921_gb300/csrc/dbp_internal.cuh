@@ -72,6 +72,7 @@ struct FwdParams {
     int single_pol;         // 1: one-polarization waveforms [n], two blocks per CTA
     int bulk_store;         // 1: outputs staged in shared memory, written by bulk copies
                             //    (out 16-byte aligned and n even; ESSFM kernels)
+    int fast_exp;           // 1: hardware exponential (ESSFM plans of at most two steps)
 };
 
 // One job of a batched launch: a plan's parameters with its own input/output buffers.

@@ -32,7 +32,7 @@ __device__ __forceinline__ void load_block(const FwdParams &p, const Blk<N> &blk
 // the previous block's last shared-memory access (and, with bulk stores, since its
 // output copy finished reading the staging buffer).  SINGLE: each lane has its own
 // intensity P = |y|^2, filter and phase.
-template <int N, bool ESSFM, bool SINGLE = false>
+template <int N, bool ESSFM, bool SINGLE = false, bool FAST = false>
 __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, int w, int b,
                                               typename Blk<N>::Regs &v) {
     using B = Blk<N>;
@@ -66,7 +66,7 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
             for (int i = 0; i < B::C1; ++i)
 #pragma unroll
                 for (int j = 0; j < B::N2; ++j) {
-                    const float2 e = expj(sT[pphys(blk.pos1(i, j))]);
+                    const float2 e = expj<FAST>(sT[pphys(blk.pos1(i, j))]);
                     v[0][i][j] = cmul(v[0][i][j], e);
                     v[1][i][j] = cmul(v[1][i][j], e);
                 }
@@ -77,14 +77,14 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
 #pragma unroll
             for (int i = 0; i < B::C1; ++i)
 #pragma unroll
-                for (int j = 0; j < B::N2; ++j) v[0][i][j] = cmul(v[0][i][j], expj(sT[pphys(blk.pos1(i, j))]));
+                for (int j = 0; j < B::N2; ++j) v[0][i][j] = cmul(v[0][i][j], expj<FAST>(sT[pphys(blk.pos1(i, j))]));
             // lane 1: its P may overwrite lane 0's (the filter is done); the barrier inside
             // essfm_theta orders the lane-0 theta reads before lane 1's theta is written
             blk.template essfm_theta<1>(v, blk.sa, p.n_tapblk);
 #pragma unroll
             for (int i = 0; i < B::C1; ++i)
 #pragma unroll
-                for (int j = 0; j < B::N2; ++j) v[1][i][j] = cmul(v[1][i][j], expj(sT[pphys(blk.pos1(i, j))]));
+                for (int j = 0; j < B::N2; ++j) v[1][i][j] = cmul(v[1][i][j], expj<FAST>(sT[pphys(blk.pos1(i, j))]));
         } else if constexpr (SINGLE) {
             const float a0 = __ldg(a);
 #pragma unroll
@@ -94,7 +94,7 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
 #pragma unroll
                     for (int j = 0; j < B::N2; ++j) {
                         const float2 y = v[l][i][j];
-                        v[l][i][j] = cmul(y, expj(a0 * fmaf(y.x, y.x, y.y * y.y)));
+                        v[l][i][j] = cmul(y, expj<FAST>(a0 * fmaf(y.x, y.x, y.y * y.y)));
                     }
         } else {
             const float a0 = __ldg(a);
@@ -103,7 +103,7 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
 #pragma unroll
                 for (int j = 0; j < B::N2; ++j) {
                     const float2 y0 = v[0][i][j], y1 = v[1][i][j];
-                    const float2 e = expj(a0 * joint_intensity(y0, y1));
+                    const float2 e = expj<FAST>(a0 * joint_intensity(y0, y1));
                     v[0][i][j] = cmul(y0, e);
                     v[1][i][j] = cmul(y1, e);
                 }
@@ -177,7 +177,7 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
 // current one is processed.  One barrier per block boundary: the steps' own barriers
 // already separate the last reads of H and of the taps from the next block's writes.  SINGLE: an item is a pair of consecutive blocks of a
 // one-polarization waveform.
-template <int N, bool ESSFM, bool SINGLE = false>
+template <int N, bool ESSFM, bool SINGLE = false, bool FAST = false>
 __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const FwdParams p, int total) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Blk<N> blk(smem_raw, threadIdx.x);
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
         load_block<N, SINGLE>(p, blk, w, b, v);
         if (ESSFM && p.bulk_store && threadIdx.x == 0) bulk_wait_read_all();
         __syncthreads();   // tables visible; previous block's shared-memory use finished
-        compute_block<N, ESSFM, SINGLE>(p, blk, w, b, v);
+        compute_block<N, ESSFM, SINGLE, FAST>(p, blk, w, b, v);
     }
     if (ESSFM && p.bulk_store && threadIdx.x == 0) bulk_wait_all();
 }
@@ -219,27 +219,32 @@ inline int resident_ctas(K kernel, int threads, size_t smem) {
     return r > 0 ? r : 1;
 }
 
-template <int N, bool ESSFM, bool SINGLE>
+template <int N, bool ESSFM, bool SINGLE, bool FAST = false>
 int launch_fwd_variant(const FwdParams &p, long long grid, cudaStream_t st) {
     using G = Geo<N>;
     static unsigned long long done = 0;
     static int resident[64];   // CTAs resident per GPU (SMs x CTAs per SM), per device
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DBP_ERR_CUDA;
-    if (!set_smem_once(dbp_fwd_kernel<N, ESSFM, SINGLE>, G::SMEM, done)) return DBP_ERR_CUDA;
-    if (!resident[dev]) resident[dev] = resident_ctas(dbp_fwd_kernel<N, ESSFM, SINGLE>, G::T, G::SMEM);
+    if (!set_smem_once(dbp_fwd_kernel<N, ESSFM, SINGLE, FAST>, G::SMEM, done)) return DBP_ERR_CUDA;
+    if (!resident[dev]) resident[dev] = resident_ctas(dbp_fwd_kernel<N, ESSFM, SINGLE, FAST>, G::T, G::SMEM);
     const int ctas = (int)(grid < resident[dev] ? grid : resident[dev]);
-    dbp_fwd_kernel<N, ESSFM, SINGLE><<<(unsigned)ctas, G::T, G::SMEM, st>>>(p, (int)grid);
+    dbp_fwd_kernel<N, ESSFM, SINGLE, FAST><<<(unsigned)ctas, G::T, G::SMEM, st>>>(p, (int)grid);
     return cudaGetLastError() == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
 }
 
+// ESSFM plans of at most two steps take the hardware exponential (expj<true>).
 template <int N>
 int launch_fwd_n(const FwdParams &p, int n_wave, bool essfm, cudaStream_t st) {
     const long long per_wave = p.single_pol ? (p.n_blocks + 1) / 2 : p.n_blocks;
     const long long grid = per_wave * n_wave;
     if (grid <= 0 || grid > 0x7fffffffLL) return DBP_ERR_ARG;
-    if (p.single_pol)
+    const bool fast = essfm && p.fast_exp;
+    if (p.single_pol) {
+        if (fast) return launch_fwd_variant<N, true, true, true>(p, grid, st);
         return essfm ? launch_fwd_variant<N, true, true>(p, grid, st) : launch_fwd_variant<N, false, true>(p, grid, st);
+    }
+    if (fast) return launch_fwd_variant<N, true, false, true>(p, grid, st);
     return essfm ? launch_fwd_variant<N, true, false>(p, grid, st) : launch_fwd_variant<N, false, false>(p, grid, st);
 }
 

@@ -373,6 +373,7 @@ void fill_fwd_params(const PlanImpl &P, FwdParams &p) {
     p.linear_only = P.method == DBP_FFE ? 1 : 0;
     p.single_pol = P.signal.n_pols == 1 ? 1 : 0;
     p.bulk_store = 0;
+    p.fast_exp = (P.method == DBP_ESSFM && P.info.n_steps <= 2) ? 1 : 0;
 }
 
 // Outputs can be written by bulk copies when every waveform's polarization rows start
