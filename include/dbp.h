@@ -195,28 +195,33 @@ int dbp_set_steps(dbp_plan_t *plan, const double *step_len_m, const double *gamm
  * Least-squares fit of a single-step ESSFM's coefficients (Section IV: the coefficients
  * minimise the mean square error between the ESSFM output and a target, e.g. the output
  * of a many-step SSFM, over a training part of the waveform).  The plan must be ESSFM
- * with n_steps = 1, FP32 precision and the fused scheme (else DBP_ERR_UNSUPPORTED); its
- * block geometry, H and gamma_eff are used as they are, its coefficients are not changed
- * (apply the result with dbp_set_coeffs).
+ * with n_steps = 1, FP32 precision, the fused scheme and two polarizations (else
+ * DBP_ERR_UNSUPPORTED); its block geometry, H and gamma_eff are used as they are, its
+ * coefficients are not changed (apply the result with dbp_set_coeffs).
  *   x, target  DEVICE complex64 [n_waveforms][2][n_samples]: the received waveforms and
  *              the targets for the plan's outputs.
  *   n_train    output samples [0, n_train) of every waveform enter the fit (<= 0: all).
- *   max_iter   Gauss-Newton updates at most (>= 0); tol: stop once every update of c
- *              is at most tol * max(1, max_i |c_i|).
+ *   max_iter   Gauss-Newton updates at most (>= 0); tol: stop once every update of the
+ *              parameters is at most tol * max(1, max |parameter|).
  *   coeffs     HOST double [n_taps + 1]: the start point on entry (c = 1, 0, ..., 0 is
- *              the SSFM), the fitted c_0..c_Nc on return (unscaled: theta = gamma_eff *
- *              sum_i c_i S_i).
+ *              the SSFM, c = 0 the linear-only compensation), the fitted c_0..c_Nc on
+ *              return (unscaled: theta = gamma_eff * sum_i c_i S_i).
+ *   phase      HOST double or NULL.  Non-NULL: a common phase phi is fitted with the
+ *              coefficients (theta + phi), start value on entry, fitted value on return;
+ *              a receiver's carrier-phase recovery removes such a phase, so the
+ *              coefficients are then not spent on matching the mean nonlinear phase.
  *   loss       HOST double [max_iter + 1] or NULL: mean over training vector samples of
  *              |t_k - z_k|^2 (both polarizations) at the start and after each update.
  *   n_iter     HOST int or NULL: updates made.
  * Uses the scratch of dbp_grad (allocated on first use); synchronizes `stream`.  The
- * normal matrix sum_k P_k S_k S_k^T does not depend on c: it is built once on the GPU
- * and factored once; each iteration is one GPU pass over the training samples.
- * Deterministic (fixed-order FP64 reductions).  DBP_ERR_SINGULAR when the normal matrix
- * is not positive definite (e.g. an all-zero input).
+ * normal matrix sum_k P_k S_k S_k^T does not depend on the parameters: it is built once
+ * on the GPU and factored once; each iteration is one GPU pass over the training
+ * samples.  Deterministic (fixed-order FP64 reductions).  DBP_ERR_SINGULAR when the
+ * normal matrix is not positive definite (e.g. an all-zero input).  The objective is
+ * not convex: different start points can end in different minima.
  */
 int dbp_fit_coeffs(dbp_plan_t *plan, const void *x, const void *target, long long n_train, int max_iter,
-                   double tol, double *coeffs, double *loss, int *n_iter, dbp_stream_t stream);
+                   double tol, double *coeffs, double *phase, double *loss, int *n_iter, dbp_stream_t stream);
 
 /*
  * As dbp_run, but in and out are HOST pointers (pinned or pageable).  The plan

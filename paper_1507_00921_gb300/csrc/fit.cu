@@ -25,7 +25,9 @@
 
 namespace dbp {
 
-__device__ __forceinline__ double regressor(const float *sP, int e, int i, int mask) {
+// S_{k,i} (i < kc), or 1 for the common-phase regressor i == kc (kc < 0: none)
+__device__ __forceinline__ double regressor(const float *sP, int e, int i, int mask, int kc) {
+    if (i == kc) return 1.0;
     return i == 0 ? (double)sP[e] : (double)sP[(e - i) & mask] + (double)sP[(e + i) & mask];
 }
 
@@ -37,8 +39,10 @@ __device__ __forceinline__ int training_count(int b, int V, long long limit) {
 
 // part[item][pair] (pairs i <= j of K regressors, row-major upper triangle) =
 // sum_k P_k S_{k,i} S_{k,j}; part[item][npair] = sum_k (P_k + |t_k,1|^2 + |t_k,2|^2).
+// Regressor kc (if >= 0) is the constant 1 of a common phase.
 __global__ void fit_gram_kernel(const float *__restrict__ Pb, const float2 *__restrict__ target, long long n, int N,
-                                int V, int half, int n_blocks, long long limit, int K, double *__restrict__ part) {
+                                int V, int half, int n_blocks, long long limit, int K, int kc,
+                                double *__restrict__ part) {
     extern __shared__ __align__(16) double dsm[];
     double *red = dsm;
     float *sP = reinterpret_cast<float *>(dsm + blockDim.x);
@@ -58,7 +62,7 @@ __global__ void fit_gram_kernel(const float *__restrict__ Pb, const float2 *__re
         double acc = 0.0;
         for (int k = 0; k < kv; ++k) {
             const int e = half + k;
-            acc += (double)sP[e] * (regressor(sP, e, i, mask) * regressor(sP, e, j, mask));
+            acc += (double)sP[e] * (regressor(sP, e, i, mask, kc) * regressor(sP, e, j, mask, kc));
         }
         part[(size_t)item * stride + pair] = acc;
     }
@@ -80,9 +84,9 @@ __global__ void fit_gram_kernel(const float *__restrict__ Pb, const float2 *__re
 }
 
 // part[item][i] = sum_k S_{k,i} Im(e^{-j theta_k} q_k), part[item][K] = sum_k Re(e^{-j theta_k} q_k),
-// theta_k = sum_i a_i S_{k,i}.
+// theta_k = sum_i a_i S_{k,i} (S_{k,kc} = 1 if kc >= 0).
 __global__ void fit_grad_kernel(const float *__restrict__ Pb, const float2 *__restrict__ q, int N, int V, int half,
-                                int n_blocks, long long limit, int K, const double *__restrict__ a,
+                                int n_blocks, long long limit, int K, int kc, const double *__restrict__ a,
                                 double *__restrict__ part) {
     extern __shared__ __align__(16) double dsm[];
     double *red = dsm;                    // [blockDim.x]
@@ -99,7 +103,7 @@ __global__ void fit_grad_kernel(const float *__restrict__ Pb, const float2 *__re
     for (int k = tid; k < kv; k += blockDim.x) {
         const int e = half + k;
         double th = 0.0;
-        for (int i = 0; i < K; ++i) th += sa[i] * regressor(sP, e, i, mask);
+        for (int i = 0; i < K; ++i) th += sa[i] * regressor(sP, e, i, mask, kc);
         double s, c;
         sincos(th, &s, &c);
         const float2 qk = q[(size_t)item * V + k];
@@ -115,7 +119,7 @@ __global__ void fit_grad_kernel(const float *__restrict__ Pb, const float2 *__re
     const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
     for (int i = warp; i < K; i += nwarps) {
         double acc = 0.0;
-        for (int k = lane; k < kv; k += 32) acc += regressor(sP, half + k, i, mask) * sw[k];
+        for (int k = lane; k < kv; k += 32) acc += regressor(sP, half + k, i, mask, kc) * sw[k];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) part[(size_t)item * (K + 1) + i] = acc;
     }
@@ -192,7 +196,8 @@ static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 using namespace dbp;
 
 extern "C" int dbp_fit_coeffs(dbp_plan_t *plan, const void *x, const void *target, long long n_train, int max_iter,
-                              double tol, double *coeffs, double *loss, int *n_iter, dbp_stream_t stream) {
+                              double tol, double *coeffs, double *phase, double *loss, int *n_iter,
+                              dbp_stream_t stream) {
     if (!plan || !x || !target || !coeffs || max_iter < 0 || !(tol >= 0.0)) return DBP_ERR_ARG;
     PlanImpl &P = plan->impl;
     if (P.method != DBP_ESSFM || P.info.n_steps != 1 || P.precision != DBP_FP32 ||
@@ -200,7 +205,10 @@ extern "C" int dbp_fit_coeffs(dbp_plan_t *plan, const void *x, const void *targe
         return DBP_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     const int N = P.info.fft_size, V = P.info.valid, half = P.info.overlap / 2;
-    const int K = P.info.n_taps + 1, nw = P.signal.n_waveforms, nb = P.info.n_blocks;
+    const int KC = P.info.n_taps + 1;             // coefficients
+    const int K = KC + (phase ? 1 : 0);           // parameters: coefficients, then the common phase
+    const int kc = phase ? KC : -1;
+    const int nw = P.signal.n_waveforms, nb = P.info.n_blocks;
     const long long n = P.signal.n_samples;
     const long long limit = (n_train <= 0 || n_train > n) ? n : n_train;
     const long long items = (long long)nb * nw;
@@ -208,7 +216,7 @@ extern "C" int dbp_fit_coeffs(dbp_plan_t *plan, const void *x, const void *targe
     const int npair = K * (K + 1) / 2;
 
     // scratch (shared with dbp_grad): P blocks, q, Gram partials and sums, gradient
-    // partials and sums, a = gamma_eff c
+    // partials and sums, a = gamma_eff c (and the phase)
     const size_t o_p = 0, o_q = o_p + al256(sizeof(float) * (size_t)items * N);
     const size_t o_gp = o_q + al256(sizeof(float2) * (size_t)items * V);
     const size_t o_gs = o_gp + al256(sizeof(double) * (size_t)items * (npair + 1));
@@ -243,28 +251,33 @@ extern "C" int dbp_fit_coeffs(dbp_plan_t *plan, const void *x, const void *targe
         cudaFuncSetAttribute(fit_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem))
         return DBP_ERR_CUDA;
     fit_gram_kernel<<<(int)items, threads, gram_smem, st>>>(Pb, (const float2 *)target, n, N, V, half, nb, limit, K,
-                                                             gpart);
+                                                             kc, gpart);
     fit_reduce_kernel<<<npair + 1, 256, 0, st>>>(gpart, items, npair + 1, gsum);
     std::vector<double> hg(npair + 1);
     if (cudaMemcpyAsync(hg.data(), gsum, sizeof(double) * (npair + 1), cudaMemcpyDeviceToHost, st) ||
         cudaStreamSynchronize(st))
         return DBP_ERR_CUDA;
 
+    // theta = gamma_eff sum_i c_i S_i (+ phase): parameter i scales its regressor by s_i
     const double ge = P.step_geff[0];
+    std::vector<double> sfac(K, ge);
+    if (phase) sfac[KC] = 1.0;
     const double m = (double)limit * nw;   // training vector samples
     std::vector<double> G((size_t)K * K), L;
     for (int i = 0, pr = 0; i < K; ++i)
-        for (int j = i; j < K; ++j, ++pr) G[(size_t)i * K + j] = G[(size_t)j * K + i] = ge * ge * hg[pr];
+        for (int j = i; j < K; ++j, ++pr) G[(size_t)i * K + j] = G[(size_t)j * K + i] = sfac[i] * sfac[j] * hg[pr];
     const double energy = hg[npair];
     if (!cholesky(G, K, L)) return DBP_ERR_SINGULAR;
 
-    std::vector<double> c(coeffs, coeffs + K), a(K), r(K + 1);
+    std::vector<double> c(K), a(K), r(K + 1);
+    for (int i = 0; i < KC; ++i) c[i] = coeffs[i];
+    if (phase) c[KC] = *phase;
     int updates = 0;
     bool done = false;
     for (int it = 0;; ++it) {
-        for (int i = 0; i < K; ++i) a[i] = ge * c[i];
+        for (int i = 0; i < K; ++i) a[i] = sfac[i] * c[i];
         if (cudaMemcpyAsync(d_a, a.data(), sizeof(double) * K, cudaMemcpyHostToDevice, st)) return DBP_ERR_CUDA;
-        fit_grad_kernel<<<(int)items, threads, grad_smem, st>>>(Pb, q, N, V, half, nb, limit, K, d_a, rpart);
+        fit_grad_kernel<<<(int)items, threads, grad_smem, st>>>(Pb, q, N, V, half, nb, limit, K, kc, d_a, rpart);
         fit_reduce_kernel<<<K + 1, 256, 0, st>>>(rpart, items, K + 1, rsum);
         if (cudaMemcpyAsync(r.data(), rsum, sizeof(double) * (K + 1), cudaMemcpyDeviceToHost, st) ||
             cudaStreamSynchronize(st))
@@ -272,7 +285,7 @@ extern "C" int dbp_fit_coeffs(dbp_plan_t *plan, const void *x, const void *targe
         if (loss) loss[it] = (energy - 2.0 * r[K]) / m;
         if (done || it == max_iter) break;
         std::vector<double> delta(r.begin(), r.begin() + K);
-        for (int i = 0; i < K; ++i) delta[i] *= ge;
+        for (int i = 0; i < K; ++i) delta[i] *= sfac[i];
         cholesky_solve(L, K, delta);
         double dmax = 0.0, cmax = 1.0;
         for (int i = 0; i < K; ++i) {
@@ -283,7 +296,8 @@ extern "C" int dbp_fit_coeffs(dbp_plan_t *plan, const void *x, const void *targe
         ++updates;
         done = dmax <= tol * cmax;
     }
-    for (int i = 0; i < K; ++i) coeffs[i] = c[i];
+    for (int i = 0; i < KC; ++i) coeffs[i] = c[i];
+    if (phase) *phase = c[KC];
     if (n_iter) *n_iter = updates;
     return DBP_OK;
 }

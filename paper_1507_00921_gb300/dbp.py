@@ -197,13 +197,16 @@ class Plan:
             self.info.step_gamma_eff = ge.copy()
 
     def fit_coeffs(self, x, target, n_train=None, max_iter: int = 20, tol: float = 1e-12, coeffs0=None,
-                   stream=None):
+                   common_phase: bool = False, phase0: float = 0.0, stream=None):
         """Section IV least-squares fit of this single-step ESSFM plan's coefficients
         against ``target`` (same layout as ``x``; e.g. a many-step SSFM output), over the
         first ``n_train`` output samples of every waveform.  Gauss-Newton from ``coeffs0``
-        (default the SSFM, c = 1, 0, ..., 0).  Returns ``(coeffs float64 [n_taps + 1],
-        losses)``, losses the mean |t - z|^2 per training vector sample at the start and
-        after each update.  The plan's own coefficients are not changed."""
+        (default the SSFM, c = 1, 0, ..., 0; c = 0 is the linear-only compensation).
+        ``common_phase``: fit a common phase with the coefficients (what a receiver's
+        carrier-phase recovery removes), starting at ``phase0``.  Returns ``(coeffs
+        float64 [n_taps + 1], losses)``, or ``(coeffs, losses, phase)`` with
+        ``common_phase``; losses are the mean |t - z|^2 per training vector sample at the
+        start and after each update.  The plan's own coefficients are not changed."""
         import torch
         self._check_tensor(x, "x")
         self._check_tensor(target, "target")
@@ -212,15 +215,18 @@ class Plan:
         c[0] = 1.0
         if coeffs0 is not None:
             c[:] = np.asarray(coeffs0, dtype=np.float64).reshape(k)
+        ph = np.array([float(phase0)], dtype=np.float64)
         losses = np.zeros(max_iter + 1, dtype=np.float64)
         n_iter = C.c_int(0)
         st = torch.cuda.current_stream(self.device) if stream is None else stream
         dp = C.POINTER(C.c_double)
         rc = self._lib.dbp_fit_coeffs(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(target.data_ptr()),
                                       int(n_train or 0), int(max_iter), float(tol), c.ctypes.data_as(dp),
-                                      losses.ctypes.data_as(dp), C.byref(n_iter), C.c_void_p(st.cuda_stream))
+                                      ph.ctypes.data_as(dp) if common_phase else dp(), losses.ctypes.data_as(dp),
+                                      C.byref(n_iter), C.c_void_p(st.cuda_stream))
         _lib.check(rc, "dbp_fit_coeffs")
-        return c, [float(v) for v in losses[:n_iter.value + 1]]
+        out = [float(v) for v in losses[:n_iter.value + 1]]
+        return (c, out, float(ph[0])) if common_phase else (c, out)
 
     def set_coeffs(self, coeffs):
         c = np.ascontiguousarray(coeffs, dtype=np.float32)

@@ -56,14 +56,19 @@ def fit_adam(plan, x, symbols, coeffs0=None, n_iter: int = 200, lr: float = 2e-3
 
 
 def fit_gauss_newton(link: dict, fs: float, x, target, n_taps: int, fft_size: int, n_train=None,
-                     max_iter: int = 20, overlap: int = 0, boundary: str = "periodic"):
+                     max_iter: int = 20, overlap: int = 0, boundary: str = "periodic", coeffs0=None,
+                     common_phase: bool = False):
     """Section IV fit of a single-step ESSFM with N_c = ``n_taps`` and block length
     ``fft_size`` to ``target`` (minimum MSE, Gauss-Newton, on the GPU through
-    dbp_fit_coeffs).  x, target: CUDA complex64 [n_waveforms, 2, n] or [2, n].
-    Returns ``(coeffs float64 [n_taps + 1], losses)``."""
+    dbp_fit_coeffs) from ``coeffs0`` (default the SSFM, c = 1, 0, ..., 0; c = 0 is the
+    linear-only compensation), optionally with a common phase fitted alongside
+    (``common_phase``).  x, target: CUDA complex64 [n_waveforms, 2, n] or [2, n].
+    Returns ``(coeffs float64 [n_taps + 1], losses)`` (``(coeffs, losses, phase)`` with
+    ``common_phase``)."""
     from .dbp import Plan
     xs = x if x.dim() == 3 else x.unsqueeze(0)
     ts = target if target.dim() == 3 else target.unsqueeze(0)
     with Plan(link, fs, xs.shape[-1], n_waveforms=xs.shape[0], method="essfm", n_steps=1, n_taps=n_taps,
               fft_size=fft_size, overlap=overlap, boundary=boundary) as plan:
-        return plan.fit_coeffs(xs.contiguous(), ts.contiguous(), n_train=n_train, max_iter=max_iter)
+        return plan.fit_coeffs(xs.contiguous(), ts.contiguous(), n_train=n_train, max_iter=max_iter, coeffs0=coeffs0,
+                               common_phase=common_phase)

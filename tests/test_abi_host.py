@@ -102,7 +102,7 @@ def test_null_arguments_and_strerror():
     assert lib.dbp_batch_run(None, None) == _lib.DBP_ERR_ARG
     assert lib.dbp_batch_publish(None, 0, None) == _lib.DBP_ERR_ARG
     assert lib.dbp_batch_status(None) == _lib.DBP_ERR_ARG
-    assert lib.dbp_fit_coeffs(None, None, None, 0, 10, 0.0, None, None, None, None) == _lib.DBP_ERR_ARG
+    assert lib.dbp_fit_coeffs(None, None, None, 0, 10, 0.0, None, None, None, None, None) == _lib.DBP_ERR_ARG
     lib.dbp_batch_destroy(None)
     lib.dbp_destroy(None)
     for code in range(-9, 1):

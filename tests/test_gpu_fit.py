@@ -137,3 +137,32 @@ def test_gauss_newton_fit_on_gpu_recovers_known_coefficients():
     assert np.max(np.abs(c_gpu - c_true)) <= 1e-4
     assert losses[-1] <= 1e-7 * energy
     assert losses[-1] < 1e-3 * losses[0]
+
+
+def test_gauss_newton_fit_with_common_phase_recovers_coefficients_and_phase():
+    """Section IV fit with a common phase fitted alongside (what carrier-phase recovery
+    removes): the noise-free target is the FP64 oracle's single-step ESSFM output with
+    known coefficients, rotated by a known phase; the fit must return both."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import dbp as odbp
+    from oracle import fiber
+    from paper_1507_00921_gb300.fit import fit_gauss_newton
+    link = synth.link(10)
+    nc, fft = 6, 1024
+    tx, _, _ = synth.pm_qpsk_waveform(2 ** 12, synth.BASE_SEED + 997, 2.0)
+    r = olink.forward(tx, link, FS, steps_per_span=20, ase_seed=synth.BASE_SEED + 998)
+    r32 = r.astype(np.complex64)
+    c_true = np.array([0.3, 0.18, 0.1, 0.05, 0.02, 0.01, 0.005])
+    phi_true = 0.7
+    cfg = fiber.make_config(link, FS, 1, nc, fft, coeffs=c_true)
+    target = odbp.dbp(r32.astype(np.complex128), cfg) * np.exp(1j * phi_true)
+    for c0 in (None, np.zeros(nc + 1)):
+        c_gpu, losses, phi = fit_gauss_newton(link, FS, torch.from_numpy(r32).cuda(),
+                                              torch.from_numpy(target.astype(np.complex64)).cuda(), nc, fft,
+                                              coeffs0=c0, common_phase=True)
+        print(f"\nstart {'SSFM' if c0 is None else 'zero'}: c {np.round(c_gpu, 5)}, phase {phi:.6f}, "
+              f"loss {losses[0]:.3e} -> {losses[-1]:.3e}")
+        assert np.max(np.abs(c_gpu - c_true)) <= 1e-4
+        assert abs(phi - phi_true) <= 1e-4
