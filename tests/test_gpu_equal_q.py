@@ -59,3 +59,43 @@ def test_essfm_single_step_against_ssfm_step_counts():
     assert q["ssfm40"] > q["ssfm20"] > q["ssfm10"]
     assert q["essfm1_nc32_phase"] >= q["ffe"] - 0.1
     assert q["essfm1_nc8_phase"] >= q["ffe"] - 0.1
+
+
+def test_multi_step_essfm_reaches_20_step_ssfm():
+    """Equal Q with a few ESSFM steps: coefficients shared by all steps, fitted with Adam
+    through the adjoint on the symbol MSE (Section IV footnote) on two training waveforms;
+    Q on a third.  On this link ESSFM with N_s = 4 (N_c = 32) must beat 20-step SSFM, and
+    each added ESSFM step must help."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_00921_gb300 import Plan
+    from paper_1507_00921_gb300.fit import fit_adam
+    link = synth.link(SPANS)
+    waves = []
+    for k in range(3):
+        tx, sym, bits = synth.pm_qpsk_waveform(2 ** 14, synth.BASE_SEED + 1600 + k, DBM)
+        r = olink.forward(tx, link, FS, steps_per_span=FWD_STEPS, ase_seed=synth.BASE_SEED + 1650 + k)
+        waves.append((r.astype(np.complex64), sym.astype(np.complex64), bits))
+    n = waves[0][0].shape[-1]
+    xtr = torch.from_numpy(np.stack([w[0] for w in waves[:2]])).cuda()
+    s_tr = torch.from_numpy(np.stack([w[1] for w in waves[:2]])).cuda()
+    xte = torch.from_numpy(waves[2][0][None]).cuda()
+
+    def q_test(**kw):
+        with Plan(link, FS, n, fft_size=FFT, **kw) as plan:
+            y = plan.run(xte)[0].cpu().numpy().astype(np.complex128)
+        return rx.evaluate(y, waves[2][1], waves[2][2])["q_db"]
+
+    q = {"ffe": q_test(method="ffe", n_steps=1), "ssfm20": q_test(method="ssfm", n_steps=20)}
+    nc = 32
+    for ns in (1, 2, 4):
+        c0 = np.full(nc + 1, 1.0 / (2 * nc + 1), dtype=np.float32)
+        with Plan(link, FS, n, n_waveforms=2, method="essfm", n_steps=ns, n_taps=nc, fft_size=FFT) as plan:
+            c, _ = fit_adam(plan, xtr, s_tr, coeffs0=c0, n_iter=300, lr=1e-2)
+        q[f"essfm{ns}"] = q_test(method="essfm", n_steps=ns, n_taps=nc, coeffs=c)
+    print(f"\n3200 km, {DBM} dBm, N_c = {nc}, Adam-fitted, test Q (dB): "
+          + ", ".join(f"{k} {v:.2f}" for k, v in q.items()))
+    assert q["essfm4"] > q["ssfm20"]
+    assert q["essfm4"] > q["essfm2"] > q["essfm1"] - 0.05
+    assert q["essfm1"] >= q["ffe"] - 0.1
