@@ -1,5 +1,5 @@
-// Fused overlap-save DBP kernel: one CTA per block of N vector samples, all N_s steps
-// in shared memory / registers, FP32.
+// Fused overlap-save DBP kernel: persistent CTAs, each taking one block of N vector
+// samples at a time through all N_s steps in shared memory / registers, FP32.
 //
 // Per step s (Section II, operations (i)-(iv), inverted for backpropagation): FFT of
 // both polarizations, x H_s (Eq. 1 inverse, 1/N folded in) fused into the contiguous
@@ -10,7 +10,9 @@
 // registers in the pass-1 layout, so a step costs four shared-memory exchanges (plus two
 // for the ESSFM filter).  The next step's H table is prefetched into shared memory with
 // cp.async while passes 1-2 run.  Overlap-and-save (Section III): the block reads input
-// window [b V - O/2, b V - O/2 + N) and writes its central V = N - O samples.
+// window [b V - O/2, b V - O/2 + N) and writes its central V = N - O samples.  In the
+// ESSFM kernels the next block's window is prefetched into L2 by bulk prefetches and
+// the outputs leave through the block buffer by bulk shared-to-global copies.
 #pragma once
 #include "block_fft.cuh"
 
