@@ -70,6 +70,10 @@ CASES = [
     ("800km_essfm1_nc8_N2048_tiny_n", 10, 100, 1, 2.0, dict(method="essfm", n_steps=1, n_taps=8, fft_size=2048)),
     ("800km_essfm1_nc8_N1024_one_sample", 10, 1, 1, 2.0, dict(method="essfm", n_steps=1, n_taps=8, fft_size=1024)),
     ("800km_essfm_nc0_N1024", 10, 5000, 1, 2.0, dict(method="essfm", n_steps=2, n_taps=0, fft_size=1024)),
+    # largest filter (N_c = 64, every tap block) and largest step count (N_s = 1024)
+    ("3200km_essfm1_nc64_N8192_max_taps", 40, 2 ** 14 + 9, 1, 2.0,
+     dict(method="essfm", n_steps=1, n_taps=64, fft_size=8192)),
+    ("160km_ssfm1024_N512_max_steps", 2, 2000, 1, 2.0, dict(method="ssfm", n_steps=1024, fft_size=512)),
 ]
 
 
@@ -86,9 +90,14 @@ def test_parity_with_oracle(torch_cuda, case):
     cfg = oracle_cfg(link, kw, info)
     ref = odbp.dbp(x.astype(np.complex64).astype(np.complex128), cfg)
     rel_rms, max_rel = compare(got, ref)
+    # Every step multiplies by the same FP32-rounded dispersion table, whose entries are
+    # off by up to ~8.4e-8 (2^-24 in each of re, im); that error adds coherently per
+    # spectral line, so beyond ~100 steps the bound 1e-7 N_s takes over from 1e-5.
+    ns = kw.get("n_steps", 1)
+    tol_rms, tol_max = max(TOL_RMS, 1e-7 * ns), max(TOL_MAX, 4e-7 * ns)
     print(f"\n{name}: relative RMS error {rel_rms:.3e}, max error / RMS {max_rel:.3e}")
-    assert rel_rms <= TOL_RMS, (rel_rms, max_rel)
-    assert max_rel <= TOL_MAX, (rel_rms, max_rel)
+    assert rel_rms <= tol_rms, (rel_rms, max_rel)
+    assert max_rel <= tol_max, (rel_rms, max_rel)
 
 
 def test_per_step_coefficients_and_nonuniform_steps(torch_cuda):
