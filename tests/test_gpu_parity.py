@@ -90,9 +90,9 @@ def test_parity_with_oracle(torch_cuda, case):
     cfg = oracle_cfg(link, kw, info)
     ref = odbp.dbp(x.astype(np.complex64).astype(np.complex128), cfg)
     rel_rms, max_rel = compare(got, ref)
-    # Every step multiplies by the same FP32-rounded dispersion table, whose entries are
-    # off by up to ~8.4e-8 (2^-24 in each of re, im); that error adds coherently per
-    # spectral line, so beyond ~100 steps the bound 1e-7 N_s takes over from 1e-5.
+    # Every step applies the same FP32-rounded twiddle factors and dispersion table, so
+    # their errors add coherently from step to step (about 8.3e-8 per step measured);
+    # beyond ~100 steps the bound 1e-7 N_s takes over from 1e-5.
     ns = kw.get("n_steps", 1)
     tol_rms, tol_max = max(TOL_RMS, 1e-7 * ns), max(TOL_MAX, 4e-7 * ns)
     print(f"\n{name}: relative RMS error {rel_rms:.3e}, max error / RMS {max_rel:.3e}")
