@@ -27,6 +27,29 @@ static const double kPi = 3.14159265358979323846;
 static const double kC = 299792458.0;
 
 // ------------------------------------------------------------------ FP64 table kernels
+// FP32 pair for the complex value (c, s) of magnitude m (FP64): among the 3 x 3 FP32
+// values within one unit in the last place of (c, s), the one whose magnitude is
+// closest to m (ties: the nearest rounding).  Tables applied at every step and their
+// conjugates in the inverse transform then do not drift in magnitude over many steps.
+__device__ float2 round_unit(double c, double s, double m) {
+    const float c0 = (float)c, s0 = (float)s;
+    float bc = c0, bs = s0;
+    double best = fabs(sqrt((double)c0 * c0 + (double)s0 * s0) - m);
+    for (int i = -1; i <= 1; ++i)
+        for (int j = -1; j <= 1; ++j) {
+            if (i == 0 && j == 0) continue;
+            const float cc = i < 0 ? nextafterf(c0, -INFINITY) : (i > 0 ? nextafterf(c0, INFINITY) : c0);
+            const float ss = j < 0 ? nextafterf(s0, -INFINITY) : (j > 0 ? nextafterf(s0, INFINITY) : s0);
+            const double e = fabs(sqrt((double)cc * cc + (double)ss * ss) - m);
+            if (e < best) {
+                best = e;
+                bc = cc;
+                bs = ss;
+            }
+        }
+    return make_float2(bc, bs);
+}
+
 __global__ void build_h_kernel(float2 *H, int N, int n0, int n1, int n2, double beta2, double fs,
                                const double *dz, int n_tables) {
     const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -43,7 +66,7 @@ __global__ void build_h_kernel(float2 *H, int N, int n0, int n1, int n2, double 
     const double red = phi - two_pi * rint(phi / two_pi);
     double s, c;
     sincos(red, &s, &c);
-    H[(size_t)tbl * N + pidx] = make_float2((float)(c / N), (float)(s / N));
+    H[(size_t)tbl * N + pidx] = round_unit(c / N, s / N, 1.0 / N);
 }
 
 // Twiddle tables, stored k-major so that lanes reading consecutive rows for one k hit
@@ -54,19 +77,19 @@ __global__ void build_twiddle_kernel(float2 *twA, float2 *twB, float2 *tw2, int 
     if (i < 16 * n2) {                  // A[k][cl] = exp(-j 2 pi cl k / N), cl < 16
         const int k = i / 16, cl = i % 16;
         sincospi(-2.0 * (double)((cl * k) % N) / (double)N, &s, &co);
-        twA[i] = make_float2((float)co, (float)s);
+        twA[i] = round_unit(co, s, 1.0);
     }
     const int nb = n0 * n1 / 16;
     if (i < nb * n2) {                  // B[k][ch] = exp(-j 2 pi 16 ch k / N), ch < n0 n1 / 16
         const int k = i / nb, ch = i % nb;
         const long long m = (16LL * ch * k) % N;
         sincospi(-2.0 * (double)m / (double)N, &s, &co);
-        twB[i] = make_float2((float)co, (float)s);
+        twB[i] = round_unit(co, s, 1.0);
     }
     if (i < n0 * n1) {                  // W2[k1][a] = exp(-j 2 pi a k1 / (n0 n1)), a < n0
         const int k = i / n0, a = i % n0;
         sincospi(-2.0 * (double)((a * k) % (n0 * n1)) / (double)(n0 * n1), &s, &co);
-        tw2[i] = make_float2((float)co, (float)s);
+        tw2[i] = round_unit(co, s, 1.0);
     }
 }
 
