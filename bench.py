@@ -243,6 +243,7 @@ def run_ours(args):
     precision = precision_measure(torch, stream) if not args.no_extras else None
     adjoint = adjoint_measure(torch, stream) if not args.no_extras else None
     single = single_pol_measure(torch, stream, fft_e) if not args.no_extras else None
+    latency = latency_measure(torch, stream) if not args.no_extras else None
     fit = fit_measure(torch, stream, fft_e) if not args.no_extras else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -276,6 +277,7 @@ def run_ours(args):
             "precision_variants": precision,
             "adjoint": adjoint,
             "single_pol": single,
+            "latency": latency,
             "ls_fit": fit,
             "gpu_launches": args.steps,
             "clocks": clocks,
@@ -409,6 +411,25 @@ def adjoint_measure(torch, stream):
         out[f"n_steps_{ns}"] = round(nw * n / t / 1e6, 1)
     out["workload"] = "3200 km ESSFM N_c=16, N=4096, 64 x 2^17 samples, input + coefficient + gamma + dz gradients"
     out["unit"] = UNIT
+    return out
+
+
+def latency_measure(torch, stream):
+    """Configuration 1 as latency: one 800 km waveform of 2^14 symbols per polarization
+    (2 x 32768 complex64, 1 MiB in + out, L2-resident), one dbp_run per call; the time
+    of one call (CUDA events over 200 back-to-back calls) for ESSFM N_s=1 N_c=8 and
+    SSFM N_s=20 at N = 1024."""
+    from paper_1507_00921_gb300 import Plan
+    n = 2 ** 15
+    x = torch.from_numpy(synth.received_like(1, 2 ** 14, LAUNCH_DBM, seed=synth.BASE_SEED + 8, distinct=1)).cuda()
+    y = torch.empty_like(x)
+    out = {}
+    for name, kw in (("essfm1_nc8", dict(method="essfm", n_steps=1, n_taps=8, coeffs=essfm_coeffs(8))),
+                     ("ssfm20", dict(method="ssfm", n_steps=20))):
+        with Plan(synth.link(10), synth.SAMPLE_RATE, n, fft_size=1024, **kw) as plan:
+            t = time_plan(torch, lambda: plan.run(x, y, stream=stream), stream, reps=200)
+        out[name + "_us"] = round(t * 1e6, 2)
+    out["workload"] = "800 km, one waveform of 2 x 32768 complex64, N = 1024, one dbp_run per call"
     return out
 
 
