@@ -492,41 +492,45 @@ def fp32_pipe(value_msps: float, fft: int, overlap: int):
 
 
 # ---------------------------------------------------------------------- CPU oracle
-def _oracle_cfg(fft_size: int, method: str):
+def _oracle_cfg(fft_size: int, method: str, n_spans: int = N_SPANS, n_taps: int = ESSFM_TAPS):
+    """Oracle configuration: ESSFM N_s=1 with ``n_taps`` taps, or SSFM N_s=20."""
     from oracle import fiber
-    link = synth.link(N_SPANS)
+    link = synth.link(n_spans)
     if method == "essfm":
-        return fiber.make_config(link, synth.SAMPLE_RATE, 1, ESSFM_TAPS, fft_size,
-                                 coeffs=essfm_coeffs(ESSFM_TAPS).astype(np.float64))
+        return fiber.make_config(link, synth.SAMPLE_RATE, 1, n_taps, fft_size,
+                                 coeffs=essfm_coeffs(n_taps).astype(np.float64))
     return fiber.make_config(link, synth.SAMPLE_RATE, 20, 0, fft_size)
 
 
 _ORACLE_INPUTS = {}
 
 
-def _oracle_input(seed: int):
-    if seed not in _ORACLE_INPUTS:
-        _ORACLE_INPUTS[seed] = synth.received_like(1, N_SYMBOLS, LAUNCH_DBM, seed=seed, distinct=1)[0].astype(
+def _oracle_input(seed: int, n_symbols: int = N_SYMBOLS):
+    key = (seed, n_symbols)
+    if key not in _ORACLE_INPUTS:
+        _ORACLE_INPUTS[key] = synth.received_like(1, n_symbols, LAUNCH_DBM, seed=seed, distinct=1)[0].astype(
             np.complex128)
-    return _ORACLE_INPUTS[seed]
+    return _ORACLE_INPUTS[key]
 
 
-def _oracle_blocks(seconds: float, fft_size: int, method: str, seed: int, n_waves: int):
-    """Run the FP64 oracle on whole overlap-save blocks of ``n_waves`` distinct 3200 km
-    waveforms, cycling through them, for about ``seconds``; returns (output vector
-    samples, elapsed seconds, blocks)."""
+def _oracle_blocks(seconds: float, fft_size: int, method: str, seed: int, n_waves: int, n_spans: int = N_SPANS,
+                   n_symbols: int = N_SYMBOLS, n_taps: int = ESSFM_TAPS):
+    """Run the FP64 oracle on whole overlap-save blocks of ``n_waves`` distinct
+    waveforms (``n_spans`` x 80 km, ``n_symbols`` symbols), cycling through them, for
+    about ``seconds``; returns (output vector samples, elapsed seconds, blocks)."""
     from oracle import dbp as odbp
-    cfg = _oracle_cfg(fft_size, method)
-    xs = [_oracle_input(seed + k) for k in range(n_waves)]
-    v, nb, _ = odbp.block_layout(N_SAMPLES, cfg.fft_size, cfg.overlap)
+    cfg = _oracle_cfg(fft_size, method, n_spans, n_taps)
+    xs = [_oracle_input(seed + k, n_symbols) for k in range(n_waves)]
+    v, nb, _ = odbp.block_layout(n_symbols * synth.SPS, cfg.fft_size, cfg.overlap)
     odbp.dbp_blocks(xs[0], cfg, np.arange(1))          # warm-up (imports, allocations)
     done, blocks, b, w = 0, 0, 0, 0
     t0 = time.perf_counter()
     while blocks == 0 or time.perf_counter() - t0 < seconds:
         ids = np.arange(b, min(nb, b + 4))
         odbp.dbp_blocks(xs[w], cfg, ids)
+        # the last block of a waveform outputs only the samples left
+        done += sum(min(v, n_symbols * synth.SPS - int(i) * v) for i in ids)
         blocks += len(ids)
-        done += len(ids) * v
         b += len(ids)
         if b >= nb:
             b, w = 0, (w + 1) % n_waves
@@ -563,10 +567,27 @@ def oracle_rate_all_cores(seconds: float, fft_size: int, method: str = "essfm"):
     return done / el, procs, f"{procs} processes x about {seconds:.1f} s, {blocks} blocks (N={fft_size}), {method}"
 
 
+# The other oracle timings reported beside the headline one: (label, spans, symbols,
+# method, taps, block length, share of the time budget).
+ORACLE_OTHERS = (
+    ("3200 km SSFM N_s=20, N=8192, 2x524288-sample waveforms", N_SPANS, N_SYMBOLS, "ssfm", 0, 8192, 0.2),
+    ("800 km (configuration 1) ESSFM N_s=1 N_c=8, N=1024, 2x32768-sample waveforms", 10, 2 ** 14, "essfm", 8, 1024,
+     0.1),
+    ("800 km (configuration 1) SSFM N_s=20, N=1024, 2x32768-sample waveforms", 10, 2 ** 14, "ssfm", 0, 1024, 0.1),
+)
+
+
 def cpu_baseline(seconds: float, fft_size: int):
     rate, sample = oracle_rate(seconds, fft_size)
     out = {"value": round(rate / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": sample + "; numpy float64, single thread"}
+    others = []
+    for label, spans, symbols, method, taps, fft, share in ORACLE_OTHERS:
+        done, el, blocks = _oracle_blocks(max(1.0, share * seconds), fft, method, synth.BASE_SEED + 3, 1, spans,
+                                          symbols, taps)
+        others.append({"workload": label, "value": round(done / el / 1e6, 4), "unit": UNIT, "cores": 1,
+                       "sample": f"{blocks} blocks, {done} output vector samples, {el:.1f} s"})
+    out["others"] = others
     try:
         per = max(1.0, seconds / 8)
         rate_all, procs, sample_all = oracle_rate_all_cores(per, fft_size)
