@@ -148,6 +148,10 @@ struct Blk {
     // float views of the block buffer for the nonlinear sub-step (valid while the block
     // is in registers): k = 0 joint intensity, 1 phase, 2 (adjoint) phase gradient.
     __device__ __forceinline__ float *farr(int k) const { return reinterpret_cast<float *>(xs) + k * G::PADP; }
+    // The forward kernels' layout instead: P at logical positions [-HALO, N + HALO)
+    // (pphys(e + HALO)), the positions outside [0, N) holding circular copies, then theta.
+    __device__ __forceinline__ float *phalo() const { return reinterpret_cast<float *>(xs); }
+    __device__ __forceinline__ float *tharr() const { return reinterpret_cast<float *>(xs) + G::PADPH; }
 
     __device__ __forceinline__ int pos1(int i, int j) const { return (t + T * i) + S1 * j; }
 
@@ -410,6 +414,54 @@ struct Blk {
         for (int q = 0; q < 4; ++q) pt[q] = make_float4(th[4 * q], th[4 * q + 1], th[4 * q + 2], th[4 * q + 3]);
     }
 
+    // fir16 reading P from the haloed layout (phalo), so that no window index wraps: every
+    // window is at a fixed offset from the thread's own positions.  With k0 = 16 t and
+    // k0 + HALO a multiple of 16, the float at logical k0 + x sits x + 4 floor(x / 16)
+    // floats after the one at k0; the windows of tap block 2m + b are those of tap block
+    // b moved by 16 m positions (20 m floats), so the tap blocks run in pairs with
+    // constant offsets.
+    static __host__ __device__ constexpr int hoff(int x) { return x + 4 * (x >= 0 ? x / 16 : -((15 - x) / 16)); }
+    template <int PAR>
+    __device__ __forceinline__ void fir16h_block(const float *pl, const float *pr, const float *a, float (&th)[16]) const {
+        float lw[24], rw[24];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const float4 fl = *reinterpret_cast<const float4 *>(pl + hoff(4 * q - 8 - 8 * PAR));
+            const float4 fr = *reinterpret_cast<const float4 *>(pr + hoff(4 * q + 8 * PAR));
+            lw[4 * q + 0] = fl.x; lw[4 * q + 1] = fl.y; lw[4 * q + 2] = fl.z; lw[4 * q + 3] = fl.w;
+            rw[4 * q + 0] = fr.x; rw[4 * q + 1] = fr.y; rw[4 * q + 2] = fr.z; rw[4 * q + 3] = fr.w;
+        }
+#pragma unroll
+        for (int ii = 1; ii <= 8; ++ii) {
+            const float ai = a[ii];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) th[r] = fmaf(ai, lw[r - ii + 8] + rw[r + ii], th[r]);
+        }
+    }
+    __device__ __forceinline__ void fir16h(const float *srch, float *dst, const float *a, int n_tapblk) const {
+        const int k0 = 16 * t;
+        const float *pc = srch + pphys(k0 + G::HALO);
+        float th[16];
+        {
+            const float a0 = a[0];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 f = reinterpret_cast<const float4 *>(pc)[q];
+                th[4 * q + 0] = a0 * f.x;
+                th[4 * q + 1] = a0 * f.y;
+                th[4 * q + 2] = a0 * f.z;
+                th[4 * q + 3] = a0 * f.w;
+            }
+        }
+        for (int m = 0; 2 * m < n_tapblk; ++m) {
+            fir16h_block<0>(pc - 20 * m, pc + 20 * m, a + 16 * m, th);
+            if (2 * m + 1 < n_tapblk) fir16h_block<1>(pc - 20 * m, pc + 20 * m, a + 16 * m + 8, th);
+        }
+        float4 *pt = reinterpret_cast<float4 *>(dst + pphys(k0));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pt[q] = make_float4(th[4 * q], th[4 * q + 1], th[4 * q + 2], th[4 * q + 3]);
+    }
+
     // The same filter on the tensor cores, for all N positions of the block: with
     // NCP = 8 n_tapblk taps a side, output group q (positions 16q..16q+15) is
     //   theta[16q + r] = sum_u W[q][u] B[u][r],  W[q][u] = src[16q - NCP + u] (circular),
@@ -480,6 +532,35 @@ struct Blk {
     // barrier, with theta visible to all threads.  LANE < 0: P is the joint intensity of
     // the two polarizations; LANE = 0 or 1: P = |y|^2 of that lane alone (one-polarization
     // blocks, the scalar form that Eq. 3 extends).
+    // essfm_theta for the forward kernels: P into the haloed layout (positions within HALO
+    // of either end written twice), the filter by fir16h, theta into tharr().
+    template <int LANE = -1>
+    __device__ __forceinline__ void essfm_theta_fwd(const Regs &v, const float *a, int n_tapblk) {
+        float *sP = phalo();
+#pragma unroll
+        for (int i = 0; i < C1; ++i)
+#pragma unroll
+            for (int j = 0; j < N2; ++j) {
+                float pk;
+                if constexpr (LANE < 0) {
+                    pk = joint_intensity(v[0][i][j], v[1][i][j]);
+                } else {
+                    const float2 y = v[LANE][i][j];
+                    pk = fmaf(y.x, y.x, y.y * y.y);
+                }
+                const int e = pos1(i, j);
+                sP[pphys(e + G::HALO)] = pk;
+                // e = t + T i + S1 j with S1 >= HALO: only j = 0 (and i = 0 when T >= HALO)
+                // can fall in the first HALO positions, only the last j (and i) in the last
+                if (j == 0 && (T < G::HALO || i == 0) && e < G::HALO) sP[pphys(e + N + G::HALO)] = pk;
+                if (j == N2 - 1 && (T < G::HALO || i == C1 - 1) && e >= N - G::HALO)
+                    sP[pphys(e - N + G::HALO)] = pk;
+            }
+        __syncthreads();
+        fir16h(sP, tharr(), a, n_tapblk);
+        __syncthreads();
+    }
+
     template <int LANE = -1>
     __device__ __forceinline__ void essfm_theta(const Regs &v, const float *a, int n_tapblk) {
         float *sP = farr(0);

@@ -26,6 +26,9 @@ struct Geo {
     static constexpr int PADX = N + N / N0;          // float4 slots of the block buffer
     static constexpr int PADP = N + 4 * (N / 16);    // floats of P / theta (+16 B per 16)
     static constexpr int PADH = N + 2 * (N / N0);    // float2 of the H table (+16 B per N0)
+    // P with circular copies of HALO samples on each side (forward filter), then theta
+    static constexpr int HALO = ((8 * ((DBP_MAX_TAPS + 7) / 8) + 15) / 16) * 16;
+    static constexpr int PADPH = (N + 2 * HALO) + 4 * ((N + 2 * HALO) / 16);
     static constexpr int TWA = 16 * N2;
     static constexpr int TWB = (S1 / 16) * N2;
     static constexpr int TW2 = N0 * N1;
@@ -38,6 +41,8 @@ struct Geo {
     static constexpr size_t SMEM = OFF_TAPS + (size_t)TAPS_MAX * 4;
     static constexpr int MINB = (512 / T) > 0 ? (512 / T) : 1;
     static_assert(2 * PADP * 4 <= PADX * 16, "P/theta must fit in the block buffer");
+    static_assert((PADPH + PADP) * 4 <= PADX * 16 && HALO <= N, "haloed P/theta must fit in the block buffer");
+    static_assert(N0 * N1 >= HALO, "the halo copies come from the first and last pass-1 rows");
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
 

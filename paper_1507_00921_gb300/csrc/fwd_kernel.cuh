@@ -62,8 +62,8 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
         const float *__restrict__ a = p.taps + p.taps_stride * s;
         if constexpr (ESSFM && !SINGLE) {
             __syncthreads();   // block buffer free: P and theta reuse it
-            blk.essfm_theta(v, blk.sa, p.n_tapblk);
-            const float *sT = blk.farr(1);
+            blk.essfm_theta_fwd(v, blk.sa, p.n_tapblk);
+            const float *sT = blk.tharr();
 #pragma unroll
             for (int i = 0; i < B::C1; ++i)
 #pragma unroll
@@ -73,16 +73,16 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
                     v[1][i][j] = cmul(v[1][i][j], e);
                 }
         } else if constexpr (ESSFM) {
-            const float *sT = blk.farr(1);
+            const float *sT = blk.tharr();
             __syncthreads();   // block buffer free
-            blk.template essfm_theta<0>(v, blk.sa, p.n_tapblk);
+            blk.template essfm_theta_fwd<0>(v, blk.sa, p.n_tapblk);
 #pragma unroll
             for (int i = 0; i < B::C1; ++i)
 #pragma unroll
                 for (int j = 0; j < B::N2; ++j) v[0][i][j] = cmul(v[0][i][j], expj<FAST>(sT[pphys(blk.pos1(i, j))]));
             // lane 1: its P may overwrite lane 0's (the filter is done); the barrier inside
             // essfm_theta orders the lane-0 theta reads before lane 1's theta is written
-            blk.template essfm_theta<1>(v, blk.sa, p.n_tapblk);
+            blk.template essfm_theta_fwd<1>(v, blk.sa, p.n_tapblk);
 #pragma unroll
             for (int i = 0; i < B::C1; ++i)
 #pragma unroll
