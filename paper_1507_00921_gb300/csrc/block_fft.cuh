@@ -414,12 +414,59 @@ struct Blk {
         for (int q = 0; q < 4; ++q) pt[q] = make_float4(th[4 * q], th[4 * q + 1], th[4 * q + 2], th[4 * q + 3]);
     }
 
-    // fir16 reading P from the haloed layout (phalo), so that no window index wraps: every
-    // window is at a fixed offset from the thread's own positions.  With k0 = 16 t and
-    // k0 + HALO a multiple of 16, the float at logical k0 + x sits x + 4 floor(x / 16)
-    // floats after the one at k0; the windows of tap block 2m + b are those of tap block
-    // b moved by 16 m positions (20 m floats), so the tap blocks run in pairs with
-    // constant offsets.
+    // fir16 reading P from the haloed layout (phalo), so that no window index wraps.  With
+    // k0 = 16 t and k0 + HALO a multiple of 16, a window starting at logical k0 + 16 a + 8 b
+    // (b = 0 or 1) has its six float4 at 20 a + 8 b + {0, 4, 8 + 4 b, 12 + 4 b, 20, 24}
+    // floats after the thread's own first position (the layout pads 4 floats per 16).
+    __device__ __forceinline__ void fir16h(const float *srch, float *dst, const float *a, int n_tapblk) const {
+        const int k0 = 16 * t;
+        const float *pc = srch + pphys(k0 + G::HALO);
+        float th[16];
+        {
+            const float a0 = a[0];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 f = reinterpret_cast<const float4 *>(pc)[q];
+                th[4 * q + 0] = a0 * f.x;
+                th[4 * q + 1] = a0 * f.y;
+                th[4 * q + 2] = a0 * f.z;
+                th[4 * q + 3] = a0 * f.w;
+            }
+        }
+        for (int blk = 0; blk < n_tapblk; ++blk) {
+            // tap block blk: left window from k0 - 8 (blk + 1), right window from k0 + 8 blk
+            const int bl = (blk + 1) & 1, br = blk & 1;
+            const float *pl = pc + (8 * bl - 20 * ((blk + 2) >> 1));
+            const float *pr = pc + (8 * br + 20 * (blk >> 1));
+            float lw[24], rw[24];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const int ol = q < 2 ? 4 * q : (q < 4 ? 4 * q + 4 * bl : 4 * q + 4);
+                const int orr = q < 2 ? 4 * q : (q < 4 ? 4 * q + 4 * br : 4 * q + 4);
+                const float4 fl = *reinterpret_cast<const float4 *>(pl + ol);
+                const float4 fr = *reinterpret_cast<const float4 *>(pr + orr);
+                lw[4 * q + 0] = fl.x; lw[4 * q + 1] = fl.y; lw[4 * q + 2] = fl.z; lw[4 * q + 3] = fl.w;
+                rw[4 * q + 0] = fr.x; rw[4 * q + 1] = fr.y; rw[4 * q + 2] = fr.z; rw[4 * q + 3] = fr.w;
+            }
+            const float *ab = a + 8 * blk;
+#pragma unroll
+            for (int ii = 1; ii <= 8; ++ii) {
+                const float ai = ab[ii];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) th[r] = fmaf(ai, lw[r - ii + 8] + rw[r + ii], th[r]);
+            }
+        }
+        float4 *pt = reinterpret_cast<float4 *>(dst + pphys(k0));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pt[q] = make_float4(th[4 * q], th[4 * q + 1], th[4 * q + 2], th[4 * q + 3]);
+    }
+
+    // fir16h with the tap blocks in pairs: the float at logical k0 + x sits x + 4 floor(x / 16)
+    // floats after the one at k0, and the windows of tap block 2m + b are those of tap
+    // block b moved by 16 m positions (20 m floats), so every offset inside a pair is a
+    // constant.  Measured faster than fir16h in the N = 8192 kernels (one CTA per SM) and
+    // slower in the shorter blocks' kernels (several CTAs per SM; by 8-10 % at N_c = 16,
+    // where the loop body of twice the length runs once per block).
     static __host__ __device__ constexpr int hoff(int x) { return x + 4 * (x >= 0 ? x / 16 : -((15 - x) / 16)); }
     template <int PAR>
     __device__ __forceinline__ void fir16h_block(const float *pl, const float *pr, const float *a, float (&th)[16]) const {
@@ -438,7 +485,7 @@ struct Blk {
             for (int r = 0; r < 16; ++r) th[r] = fmaf(ai, lw[r - ii + 8] + rw[r + ii], th[r]);
         }
     }
-    __device__ __forceinline__ void fir16h(const float *srch, float *dst, const float *a, int n_tapblk) const {
+    __device__ __forceinline__ void fir16h_pairs(const float *srch, float *dst, const float *a, int n_tapblk) const {
         const int k0 = 16 * t;
         const float *pc = srch + pphys(k0 + G::HALO);
         float th[16];
@@ -533,7 +580,7 @@ struct Blk {
     // the two polarizations; LANE = 0 or 1: P = |y|^2 of that lane alone (one-polarization
     // blocks, the scalar form that Eq. 3 extends).
     // essfm_theta for the forward kernels: P into the haloed layout (positions within HALO
-    // of either end written twice), the filter by fir16h, theta into tharr().
+    // of either end written twice), the filter by fir16h / fir16h_pairs, theta into tharr().
     template <int LANE = -1>
     __device__ __forceinline__ void essfm_theta_fwd(const Regs &v, const float *a, int n_tapblk) {
         float *sP = phalo();
@@ -557,7 +604,10 @@ struct Blk {
                     sP[pphys(e - N + G::HALO)] = pk;
             }
         __syncthreads();
-        fir16h(sP, tharr(), a, n_tapblk);
+        if constexpr (N >= 8192)
+            fir16h_pairs(sP, tharr(), a, n_tapblk);
+        else
+            fir16h(sP, tharr(), a, n_tapblk);
         __syncthreads();
     }
 
