@@ -417,19 +417,21 @@ def adjoint_measure(torch, stream):
 def latency_measure(torch, stream):
     """Configuration 1 as latency: one 800 km waveform of 2^14 symbols per polarization
     (2 x 32768 complex64, 1 MiB in + out, L2-resident), one dbp_run per call; the time
-    of one call (CUDA events over 200 back-to-back calls) for ESSFM N_s=1 N_c=8 and
+    of one call (CUDA events over 2000 back-to-back calls, clocks sampled) for ESSFM N_s=1 N_c=8 and
     SSFM N_s=20 at N = 1024."""
     from paper_1507_00921_gb300 import Plan
     n = 2 ** 15
     x = torch.from_numpy(synth.received_like(1, 2 ** 14, LAUNCH_DBM, seed=synth.BASE_SEED + 8, distinct=1)).cuda()
     y = torch.empty_like(x)
     out = {}
-    for name, kw in (("essfm1_nc8", dict(method="essfm", n_steps=1, n_taps=8, coeffs=essfm_coeffs(8))),
-                     ("ssfm20", dict(method="ssfm", n_steps=20))):
-        with Plan(synth.link(10), synth.SAMPLE_RATE, n, fft_size=1024, **kw) as plan:
-            t = time_plan(torch, lambda: plan.run(x, y, stream=stream), stream, reps=200)
-        out[name + "_us"] = round(t * 1e6, 2)
+    with ClockSampler(smi_index(torch.cuda.current_device())) as clk:
+        for name, kw in (("essfm1_nc8", dict(method="essfm", n_steps=1, n_taps=8, coeffs=essfm_coeffs(8))),
+                         ("ssfm20", dict(method="ssfm", n_steps=20))):
+            with Plan(synth.link(10), synth.SAMPLE_RATE, n, fft_size=1024, **kw) as plan:
+                t = time_plan(torch, lambda: plan.run(x, y, stream=stream), stream, reps=2000)
+            out[name + "_us"] = round(t * 1e6, 2)
     out["workload"] = "800 km, one waveform of 2 x 32768 complex64, N = 1024, one dbp_run per call"
+    out["clocks"] = clk.summary()
     return out
 
 
