@@ -157,16 +157,18 @@ def test_alias_rejected(torch_cuda):
         assert e.value.code == -6
 
 
-@pytest.mark.parametrize("method,ns,nc,fft", [("essfm", 1, 32, 4096), ("essfm", 1, 32, 8192),
-                                              ("ssfm", 20, 0, 4096)])
-def test_full_size_3200km_sampled_blocks(torch_cuda, method, ns, nc, fft):
-    """Full 3200 km workload (2 x 524288 samples per waveform, batch of 8) in the
-    launch configuration of the benchmark; sampled blocks checked against the oracle."""
+@pytest.mark.parametrize("method,ns,nc,fft,nw", [("essfm", 1, 32, 4096, 8), ("essfm", 1, 32, 8192, 8),
+                                                 ("ssfm", 20, 0, 4096, 8), ("essfm", 1, 32, 8192, 128),
+                                                 ("essfm", 2, 32, 8192, 128)])
+def test_full_size_3200km_sampled_blocks(torch_cuda, method, ns, nc, fft, nw):
+    """Full 3200 km workload (2 x 524288 samples per waveform; batches of 8, and of 128
+    as the benchmark launches it) in the benchmark's launch configuration; sampled
+    blocks of the first, a middle and the last waveform checked against the oracle."""
     from paper_1507_00921_gb300 import Plan
     torch = torch_cuda
     link = synth.link(40)
-    n, nw = 2 * 2 ** 18, 8
-    x = synth.received_like(nw, 2 ** 18, 2.0, seed=4242, distinct=2)
+    n = 2 * 2 ** 18
+    x = synth.received_like(nw, 2 ** 18, 2.0, seed=4242, distinct=4)
     coeffs = None
     if nc:
         c = 0.6 * np.exp(-np.arange(nc + 1) / 10.0)
@@ -180,7 +182,7 @@ def test_full_size_3200km_sampled_blocks(torch_cuda, method, ns, nc, fft):
     cfg = oracle_cfg(link, kw, info)
     rng = np.random.default_rng(5)
     v = info.valid
-    for w in [0, 5]:
+    for w in sorted({0, 5 * nw // 8 + 2, nw - 1}):
         ids = np.unique(np.concatenate([[0, info.n_blocks - 1], rng.integers(0, info.n_blocks, 6)]))
         ref = odbp.dbp_blocks(x[w].astype(np.complex128), cfg, ids)         # [k, 2, V]
         for j, b in enumerate(ids):
