@@ -574,13 +574,13 @@ struct Blk {
             }
     }
 
-    // ESSFM phase theta (Eq. 3) of the block in registers, into farr(1).  The block
-    // buffer must be free (a barrier after the last pass-1' read); returns after a
-    // barrier, with theta visible to all threads.  LANE < 0: P is the joint intensity of
-    // the two polarizations; LANE = 0 or 1: P = |y|^2 of that lane alone (one-polarization
-    // blocks, the scalar form that Eq. 3 extends).
-    // essfm_theta for the forward kernels: P into the haloed layout (positions within HALO
-    // of either end written twice), the filter by fir16h / fir16h_pairs, theta into tharr().
+    // ESSFM phase theta (Eq. 3) of the block in registers, for the forward kernels: P into
+    // the haloed layout (positions within HALO of either end written twice), the filter by
+    // fir16h / fir16h_pairs, theta into tharr().  The block buffer must be free (a barrier
+    // after the last pass-1' read); returns after a barrier, with theta visible to all
+    // threads.  LANE < 0: P is the joint intensity of the two polarizations; LANE = 0 or
+    // 1: P = |y|^2 of that lane alone (one-polarization blocks, the scalar form that
+    // Eq. 3 extends).
     template <int LANE = -1>
     __device__ __forceinline__ void essfm_theta_fwd(const Regs &v, const float *a, int n_tapblk) {
         float *sP = phalo();
@@ -611,6 +611,8 @@ struct Blk {
         __syncthreads();
     }
 
+    // The same with P in farr(0) (no halo, the wrapping fir16) and theta into farr(1): the
+    // adjoint's layout, which keeps a third array (the phase gradient) in the block buffer.
     template <int LANE = -1>
     __device__ __forceinline__ void essfm_theta(const Regs &v, const float *a, int n_tapblk) {
         float *sP = farr(0);
