@@ -47,6 +47,47 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *g, unsigned bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(g), "r"(bytes) : "memory");
 }
 
+// Tensor memory (TMEM) used as per-thread storage: tcgen05.alloc by one warp (the address
+// goes to shared memory), 32-bit columns of the thread's lane read and written with the
+// 32x32b shapes.  A warp reaches only the 32 lanes of its quarter of the warpgroup
+// (lanes 32 (warp % 4) ...); the lane goes in the address's upper 16 bits.
+__device__ __forceinline__ void tmem_alloc(uint32_t *smem_dst, uint32_t ncols) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(s), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+// r[0..31] -> columns taddr .. taddr + 31 of this thread's lane; returns when written
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+// columns taddr .. taddr + 7 of this thread's lane -> r[0..7]; the wait takes the
+// registers as operands so that no use is scheduled before the data has arrived
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+                 :
+                 : "memory");
+}
+
 // exp(+j theta) for the nonlinear rotation.
 // Accurate (default): theta = q pi/2 + r with a three-constant Cody-Waite reduction
 // (pi/2 = 1.5703125 + 4.837512969970703e-4 + 7.549790126404332e-8; the first two
@@ -130,6 +171,7 @@ struct Blk {
     float2 *s2;
     float *sa;     // current step's taps gamma_eff c_i (shared, broadcast reads)
     int t;
+    uint32_t twt = 0;   // TMEM address of this thread's pass-1 twiddles (twiddles_to_tmem)
 
     __device__ __forceinline__ Blk(unsigned char *smem, int tid)
         : xs(reinterpret_cast<float4 *>(smem)),
@@ -249,7 +291,44 @@ struct Blk {
         }
     }
 
-    // pass 1 (forward): DFT over the top digit, twiddle, registers -> shared memory
+    // Pass-1 twiddles W_N^{c k}, k = 1 .. N2 - 1, of a thread that owns one pass-1 column
+    // (C1 = 1, N2 = 16): computed once from the tables and kept in 32 TMEM columns of the
+    // thread's lane at twt (30 floats and two unused), so that the passes read them with
+    // four tcgen05.ld instead of two table reads and a complex product per k.
+    __device__ __forceinline__ void twiddles_to_tmem() {
+        static_assert(C1 == 1 && N2 == 16, "one pass-1 column of 16 per thread");
+        const float2 *ta = sA + (t & 15);
+        const float2 *tb = sB + (t >> 4);
+        uint32_t r[32];
+#pragma unroll
+        for (int k = 1; k < 16; ++k) {
+            const float2 wk = cmul(ta[16 * k], tb[(S1 / 16) * k]);
+            r[2 * k - 2] = __float_as_uint(wk.x);
+            r[2 * k - 1] = __float_as_uint(wk.y);
+        }
+        r[30] = r[31] = 0u;
+        tmem_st32(twt, r);
+    }
+    template <bool CONJ>
+    __device__ __forceinline__ void twiddle_tmem(float2 (&u0)[16], float2 (&u1)[16]) const {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t r[8];
+            tmem_ld8(twt + 8 * q, r);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int k = 4 * q + m + 1;
+                if (k >= 16) break;
+                const float2 wk = make_float2(__uint_as_float(r[2 * m]), __uint_as_float(r[2 * m + 1]));
+                u0[k] = CONJ ? cmulc(u0[k], wk) : cmul(u0[k], wk);
+                u1[k] = CONJ ? cmulc(u1[k], wk) : cmul(u1[k], wk);
+            }
+        }
+    }
+
+    // pass 1 (forward): DFT over the top digit, twiddle, registers -> shared memory.
+    // TM: the twiddles come from TMEM (twiddles_to_tmem).
+    template <bool TM = false>
     __device__ __forceinline__ void pass1_fwd(Regs &v) {
 #pragma unroll
         for (int i = 0; i < C1; ++i) {
@@ -258,11 +337,15 @@ struct Blk {
             const float2 *tb = sB + (c >> 4);
             Dft<N2, false>::run(v[0][i]);
             Dft<N2, false>::run(v[1][i]);
+            if constexpr (TM) {
+                twiddle_tmem<false>(v[0][i], v[1][i]);
+            } else {
 #pragma unroll
-            for (int k = 1; k < N2; ++k) {
-                const float2 wk = cmul(ta[16 * k], tb[(S1 / 16) * k]);
-                v[0][i][k] = cmul(v[0][i][k], wk);
-                v[1][i][k] = cmul(v[1][i][k], wk);
+                for (int k = 1; k < N2; ++k) {
+                    const float2 wk = cmul(ta[16 * k], tb[(S1 / 16) * k]);
+                    v[0][i][k] = cmul(v[0][i][k], wk);
+                    v[1][i][k] = cmul(v[1][i][k], wk);
+                }
             }
 #pragma unroll
             for (int k = 0; k < N2; ++k)
@@ -349,6 +432,7 @@ struct Blk {
     }
 
     // pass 1' (inverse): conjugate twiddle, inverse radix-N2 DFT, shared memory -> registers
+    template <bool TM = false>
     __device__ __forceinline__ void pass1_inv(Regs &v) const {
 #pragma unroll
         for (int i = 0; i < C1; ++i) {
@@ -361,11 +445,15 @@ struct Blk {
                 v[0][i][j] = make_float2(f.x, f.y);
                 v[1][i][j] = make_float2(f.z, f.w);
             }
+            if constexpr (TM) {
+                twiddle_tmem<true>(v[0][i], v[1][i]);
+            } else {
 #pragma unroll
-            for (int k = 1; k < N2; ++k) {
-                const float2 wk = cmul(ta[16 * k], tb[(S1 / 16) * k]);
-                v[0][i][k] = cmulc(v[0][i][k], wk);
-                v[1][i][k] = cmulc(v[1][i][k], wk);
+                for (int k = 1; k < N2; ++k) {
+                    const float2 wk = cmul(ta[16 * k], tb[(S1 / 16) * k]);
+                    v[0][i][k] = cmulc(v[0][i][k], wk);
+                    v[1][i][k] = cmulc(v[1][i][k], wk);
+                }
             }
             Dft<N2, true>::run(v[0][i]);
             Dft<N2, true>::run(v[1][i]);

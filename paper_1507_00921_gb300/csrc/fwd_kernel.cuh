@@ -34,7 +34,7 @@ __device__ __forceinline__ void load_block(const FwdParams &p, const Blk<N> &blk
 // the previous block's last shared-memory access (and, with bulk stores, since its
 // output copy finished reading the staging buffer).  SINGLE: each lane has its own
 // intensity P = |y|^2, filter and phase.
-template <int N, bool ESSFM, bool SINGLE = false, bool FAST = false>
+template <int N, bool ESSFM, bool SINGLE = false, bool FAST = false, bool TM = false>
 __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, int w, int b,
                                               typename Blk<N>::Regs &v) {
     using B = Blk<N>;
@@ -45,7 +45,7 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
     for (int s = 0; s < p.n_steps; ++s) {
         if (ESSFM && s > 0) __syncthreads();   // previous step's theta and tap reads are done
         if (ESSFM) blk.stage_taps(p.taps + p.taps_stride * s, p.taps_stride);
-        blk.pass1_fwd(v);
+        blk.template pass1_fwd<TM>(v);
         __syncthreads();
         blk.template pass2<false>();
         cp_async_wait_all();
@@ -55,7 +55,7 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
         if (p.h_stride != 0 && s + 1 < p.n_steps) blk.prefetch_h(p.H + p.h_stride * (s + 1));
         blk.template pass2<true>();
         __syncthreads();
-        blk.pass1_inv(v);
+        blk.template pass1_inv<TM>(v);
         if (p.linear_only) continue;   // FFE: dispersion compensation only
 
         // ---- nonlinear sub-step
@@ -182,8 +182,27 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
 template <int N, bool ESSFM, bool SINGLE = false, bool FAST = false>
 __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const FwdParams p, int total) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // N = 8192 (one CTA per SM, one pass-1 column per thread): each thread's pass-1
+    // twiddles live in TMEM, 32 columns of its lane; 16 warps = 4 per lane quarter, so
+    // 4 x 32 = 128 columns
+    constexpr bool TM = (N == 8192);
+    constexpr uint32_t TM_COLS = 128;
+    __shared__ uint32_t s_tmem;
     Blk<N> blk(smem_raw, threadIdx.x);
     blk.load_tables(p.twA, p.twB, p.tw2);
+    if constexpr (TM) {
+        static_assert(Geo<N>::T == 512, "16 warps: 4 per TMEM lane quarter");
+        if (threadIdx.x < 32) {
+            tmem_alloc(&s_tmem, TM_COLS);
+            tmem_relinquish();
+        }
+        tmem_fence_before_sync();
+        __syncthreads();   // tables and the TMEM address visible
+        tmem_fence_after_sync();
+        const uint32_t warp = threadIdx.x >> 5;
+        blk.twt = s_tmem + (((warp & 3u) * 32u) << 16) + 32u * (warp >> 2);
+        blk.twiddles_to_tmem();
+    }
     const int per_wave = SINGLE ? (p.n_blocks + 1) / 2 : p.n_blocks;
     const int bstep = SINGLE ? 2 : 1;
     const long long wstride = (SINGLE ? 1 : 2) * p.n;
@@ -204,9 +223,15 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
         load_block<N, SINGLE>(p, blk, w, b, v);
         if (ESSFM && p.bulk_store && threadIdx.x == 0) bulk_wait_read_all();
         __syncthreads();   // tables visible; previous block's shared-memory use finished
-        compute_block<N, ESSFM, SINGLE, FAST>(p, blk, w, b, v);
+        compute_block<N, ESSFM, SINGLE, FAST, TM>(p, blk, w, b, v);
     }
     if (ESSFM && p.bulk_store && threadIdx.x == 0) bulk_wait_all();
+    if constexpr (TM) {   // every tcgen05.ld has been waited for; free the columns
+        tmem_fence_before_sync();
+        __syncthreads();
+        tmem_fence_after_sync();
+        if (threadIdx.x < 32) tmem_dealloc(s_tmem, TM_COLS);
+    }
 }
 
 // SMs x resident CTAs per SM for a kernel configuration (at least 1).
