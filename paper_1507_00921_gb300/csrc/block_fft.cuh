@@ -291,12 +291,14 @@ struct Blk {
         }
     }
 
-    // Pass-1 twiddles W_N^{c k}, k = 1 .. N2 - 1, of a thread that owns one pass-1 column
-    // (C1 = 1, N2 = 16): computed once from the tables and kept in 32 TMEM columns of the
-    // thread's lane at twt (30 floats and two unused), so that the passes read them with
-    // four tcgen05.ld instead of two table reads and a complex product per k.
+    // Inter-pass twiddles of a thread that owns one pass-1 column and one pass-2 column
+    // (C1 = C2 = 1, N1 = N2 = 16): pass 1 W_N^{c k} and pass 2 W_{N0 N1}^{n0 k}, k = 1 .. 15,
+    // computed once from the tables and kept in 64 TMEM columns of the thread's lane at twt
+    // (pass 1 in columns 0-29, pass 2 in 32-61), so that each pass reads them with four
+    // tcgen05.ld instead of table reads (and, for pass 1, a complex product) per k.
+    static constexpr uint32_t TW_COLS = 64;
     __device__ __forceinline__ void twiddles_to_tmem() {
-        static_assert(C1 == 1 && N2 == 16, "one pass-1 column of 16 per thread");
+        static_assert(C1 == 1 && N2 == 16 && C2 == 1 && N1 == 16, "one column of 16 per thread in passes 1 and 2");
         const float2 *ta = sA + (t & 15);
         const float2 *tb = sB + (t >> 4);
         uint32_t r[32];
@@ -308,13 +310,22 @@ struct Blk {
         }
         r[30] = r[31] = 0u;
         tmem_st32(twt, r);
+        const float2 *tw = s2 + t % N0;
+#pragma unroll
+        for (int k = 1; k < 16; ++k) {
+            const float2 wk = tw[N0 * k];
+            r[2 * k - 2] = __float_as_uint(wk.x);
+            r[2 * k - 1] = __float_as_uint(wk.y);
+        }
+        tmem_st32(twt + 32, r);
     }
+    // u_k *= w_k (CONJ: conj(w_k)), k = 1 .. 15, with w from TMEM columns col ...
     template <bool CONJ>
-    __device__ __forceinline__ void twiddle_tmem(float2 (&u0)[16], float2 (&u1)[16]) const {
+    __device__ __forceinline__ void twiddle_tmem(float2 (&u0)[16], float2 (&u1)[16], uint32_t col = 0) const {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             uint32_t r[8];
-            tmem_ld8(twt + 8 * q, r);
+            tmem_ld8(twt + col + 8 * q, r);
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const int k = 4 * q + m + 1;
@@ -353,8 +364,9 @@ struct Blk {
         }
     }
 
-    // pass 2: radix N1, stride N0 (forward: DFT then twiddle; inverse: conj twiddle then IDFT)
-    template <bool INV>
+    // pass 2: radix N1, stride N0 (forward: DFT then twiddle; inverse: conj twiddle then IDFT).
+    // TM: the twiddles come from TMEM (twiddles_to_tmem).
+    template <bool INV, bool TM = false>
     __device__ __forceinline__ void pass2() {
 #pragma unroll
         for (int i = 0; i < C2; ++i) {
@@ -372,18 +384,26 @@ struct Blk {
             if constexpr (!INV) {
                 Dft<N1, false>::run(u0);
                 Dft<N1, false>::run(u1);
+                if constexpr (TM) {
+                    twiddle_tmem<false>(u0, u1, 32);
+                } else {
 #pragma unroll
-                for (int k = 1; k < N1; ++k) {
-                    const float2 wk = tw[N0 * k];
-                    u0[k] = cmul(u0[k], wk);
-                    u1[k] = cmul(u1[k], wk);
+                    for (int k = 1; k < N1; ++k) {
+                        const float2 wk = tw[N0 * k];
+                        u0[k] = cmul(u0[k], wk);
+                        u1[k] = cmul(u1[k], wk);
+                    }
                 }
             } else {
+                if constexpr (TM) {
+                    twiddle_tmem<true>(u0, u1, 32);
+                } else {
 #pragma unroll
-                for (int k = 1; k < N1; ++k) {
-                    const float2 wk = tw[N0 * k];
-                    u0[k] = cmulc(u0[k], wk);
-                    u1[k] = cmulc(u1[k], wk);
+                    for (int k = 1; k < N1; ++k) {
+                        const float2 wk = tw[N0 * k];
+                        u0[k] = cmulc(u0[k], wk);
+                        u1[k] = cmulc(u1[k], wk);
+                    }
                 }
                 Dft<N1, true>::run(u0);
                 Dft<N1, true>::run(u1);

@@ -47,13 +47,13 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
         if (ESSFM) blk.stage_taps(p.taps + p.taps_stride * s, p.taps_stride);
         blk.template pass1_fwd<TM>(v);
         __syncthreads();
-        blk.template pass2<false>();
+        blk.template pass2<false, TM && ESSFM>();
         cp_async_wait_all();
         __syncthreads();   // pass-2 results and H_s visible
         blk.pass3(mid);
         __syncthreads();
         if (p.h_stride != 0 && s + 1 < p.n_steps) blk.prefetch_h(p.H + p.h_stride * (s + 1));
-        blk.template pass2<true>();
+        blk.template pass2<true, TM && ESSFM>();
         __syncthreads();
         blk.template pass1_inv<TM>(v);
         if (p.linear_only) continue;   // FFE: dispersion compensation only
@@ -182,11 +182,13 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
 template <int N, bool ESSFM, bool SINGLE = false, bool FAST = false>
 __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const FwdParams p, int total) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // N = 8192 (one CTA per SM, one pass-1 column per thread): each thread's pass-1
-    // twiddles live in TMEM, 32 columns of its lane; 16 warps = 4 per lane quarter, so
-    // 4 x 32 = 128 columns
+    // N = 8192 (one CTA per SM, one pass-1 and one pass-2 column per thread): each
+    // thread's inter-pass twiddles live in TMEM, 64 columns of its lane; 16 warps = 4 per
+    // lane quarter, so 4 x 64 = 256 columns.  Pass 1 reads them in every kernel, pass 2 in
+    // the ESSFM kernels (in the SSFM/FFE kernels the pass-2 table reads measured faster:
+    // their register allocation spills more with the TMEM reads).
     constexpr bool TM = (N == 8192);
-    constexpr uint32_t TM_COLS = 128;
+    constexpr uint32_t TM_COLS = 4 * Blk<N>::TW_COLS;
     __shared__ uint32_t s_tmem;
     Blk<N> blk(smem_raw, threadIdx.x);
     blk.load_tables(p.twA, p.twB, p.tw2);
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const 
         __syncthreads();   // tables and the TMEM address visible
         tmem_fence_after_sync();
         const uint32_t warp = threadIdx.x >> 5;
-        blk.twt = s_tmem + (((warp & 3u) * 32u) << 16) + 32u * (warp >> 2);
+        blk.twt = s_tmem + (((warp & 3u) * 32u) << 16) + Blk<N>::TW_COLS * (warp >> 2);
         blk.twiddles_to_tmem();
     }
     const int per_wave = SINGLE ? (p.n_blocks + 1) / 2 : p.n_blocks;
