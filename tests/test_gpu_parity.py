@@ -61,6 +61,10 @@ CASES = [
     ("3200km_essfm2_nc16_N4096_zero", 40, 3 * 2600 + 7, 1, 4.0,
      dict(method="essfm", n_steps=2, n_taps=16, fft_size=4096, boundary="zero")),
     ("3200km_essfm4_nc32_N8192", 40, 2 ** 15, 1, 2.0, dict(method="essfm", n_steps=4, n_taps=32, fft_size=8192)),
+    # unequal steps: one H table per step (the N = 8192 ESSFM kernel that keeps H in
+    # shared memory; equal steps keep one H in tensor memory)
+    ("3200km_essfm3_nc16_N8192_unequal_steps", 40, 2 ** 15 + 77, 2, 2.0,
+     dict(method="essfm", n_steps=3, n_taps=16, fft_size=8192, step_len_m=np.array([1.4e6, 1.0e6, 0.8e6]))),
     ("3200km_ssfm1_N8192_zero", 40, 20000, 2, 6.0, dict(method="ssfm", n_steps=1, fft_size=8192, boundary="zero")),
     ("3200km_ssfm5_N2048", 40, 5000, 3, 0.0, dict(method="ssfm", n_steps=5, fft_size=2048)),
     ("3200km_ssfm20_N4096", 40, 2 ** 14, 1, 2.0, dict(method="ssfm", n_steps=20, fft_size=4096)),
