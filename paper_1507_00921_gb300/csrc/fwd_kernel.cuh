@@ -12,7 +12,8 @@
 // cp.async while passes 1-2 run.  Overlap-and-save (Section III): the block reads input
 // window [b V - O/2, b V - O/2 + N) and writes its central V = N - O samples.  In the
 // ESSFM kernels the next block's window is prefetched into L2 by bulk prefetches and
-// the outputs leave through the block buffer by bulk shared-to-global copies.
+// the outputs leave through the block buffer by bulk shared-to-global copies.  At
+// N = 8192 the inter-pass twiddles of each thread sit in tensor memory (tcgen05).
 #pragma once
 #include "block_fft.cuh"
 
@@ -174,11 +175,12 @@ __device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, i
 }
 
 // Persistent over blocks: CTA c processes blocks c, c + gridDim.x, ...  The twiddle
-// tables (and H when all steps share it) are loaded into shared memory once per CTA;
-// the input window of the block this CTA runs next is prefetched into L2 while the
-// current one is processed.  One barrier per block boundary: the steps' own barriers
-// already separate the last reads of H and of the taps from the next block's writes.  SINGLE: an item is a pair of consecutive blocks of a
-// one-polarization waveform.
+// tables (and H when all steps share it) are loaded into shared memory once per CTA, and
+// at N = 8192 each thread's inter-pass twiddles once into tensor memory; the input
+// window of the block this CTA runs next is prefetched into L2 while the current one is
+// processed.  One barrier per block boundary: the steps' own barriers already separate
+// the last reads of H and of the taps from the next block's writes.  SINGLE: an item is
+// a pair of consecutive blocks of a one-polarization waveform.
 template <int N, bool ESSFM, bool SINGLE = false, bool FAST = false>
 __global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB) dbp_fwd_kernel(const FwdParams p, int total) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
