@@ -72,7 +72,8 @@ struct FwdParams {
     const float2 *twA;      // [N2][16] W_N^{cl k}
     const float2 *twB;      // [N2][N0 N1 / 16] W_{N/16}^{ch k}
     const float2 *tw2;      // [N1][N0] W_{N0 N1}^{n0 k1}
-    int prefetch_ahead;     // blocks ahead whose input window is prefetched into L2 (0: off)
+    int prefetch_ahead;     // nonzero: each CTA prefetches into L2 the input window of the block it
+                            // runs next, one wave of the persistent grid ahead (0: off)
     int linear_only;        // 1: skip the nonlinear sub-step (FFE)
     int single_pol;         // 1: one-polarization waveforms [n], two blocks per CTA
     int bulk_store;         // 1: outputs staged in shared memory, written by bulk copies
@@ -98,7 +99,7 @@ struct PlanImpl {
     int n_tapblk;
     int taps_stride;
     bool h_shared;            // all steps share one H table
-    int prefetch_ahead = -1;  // L2 prefetch distance in blocks (-1: one wave of resident CTAs)
+    int prefetch_ahead = 1;   // L2 prefetch of the next block's window (0: off)
     int precision = DBP_FP32;
     int scheme = DBP_SCHEME_FUSED;
     int user_overlap = 0;
