@@ -120,3 +120,23 @@ def test_run_batch_one_shot(torch_cuda):
         torch.cuda.synchronize()
         assert (y - r).abs().max().item() <= 1e-6 * r.abs().max().item()
         p.close()
+
+
+def test_tensor_memory_twiddles_match_table_twiddles(torch_cuda):
+    """At N = 8192 the forward kernel reads each thread's pass-1 twiddles from tensor
+    memory, where they were stored once per kernel; the batch kernel forms them from the
+    shared-memory tables every pass.  Both take the same FP32 product, so for an SSFM
+    plan (which differs in nothing else) the two outputs are bit for bit identical."""
+    torch = torch_cuda
+    from paper_1507_00921_gb300 import Batch, Plan
+    n, nw = 20000, 2
+    x = torch.from_numpy(synth.random_field(nw, n, synth.dbm_to_w(2.0), seed=818).astype(np.complex64)).cuda()
+    with Plan(synth.link(40), FS, n, n_waveforms=nw, method="ssfm", n_steps=2, fft_size=8192) as plan:
+        y_run = plan.run(x)
+        y_batch = torch.zeros_like(x)
+        batch = Batch([plan], [x], [y_batch])
+        batch.run()
+        torch.cuda.synchronize()
+        assert batch.status() == 0
+        batch.close()
+    assert torch.equal(y_run, y_batch)
