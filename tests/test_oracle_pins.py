@@ -153,6 +153,78 @@ def test_link_exact_inverse_recovers_tx():
     assert rel(back, tx) < 1e-11
 
 
+def test_substep_effective_length_quadrature_and_limit():
+    """The forward simulator's nonlinear weight of a sub-step of length h is the integral
+    over the sub-step of the power relative to its midpoint value (Strang splitting with
+    the rotation at the midpoint), exp(alpha h/2)(1 - exp(-alpha h))/alpha: checked
+    against numerical quadrature of exp(-alpha (z - h/2)) over [0, h], and its alpha -> 0
+    limit h."""
+    from scipy.integrate import quad
+    alpha = fiber.alpha_per_m(0.2)
+    for h in (80.0, 3.2e3, 8e3, 80e3):
+        want, _ = quad(lambda z: math.exp(-alpha * (z - h / 2.0)), 0.0, h, epsabs=0, epsrel=1e-13)
+        assert abs(olink._mid_heff(alpha, h) - want) <= 1e-12 * want
+    assert olink._mid_heff(0.0, 8e3) == 8e3
+    for a in (1e-9, 1e-12):
+        assert abs(olink._mid_heff(a, 8e3) - 8e3) < 1e-6 * 8e3
+
+
+def test_forward_cw_nonlinear_phase_is_gamma_p_leff():
+    """Section II: a constant-envelope (CW) field is untouched by dispersion, so one span of
+    the forward simulator rotates it by exactly -gamma m P_0 L_eff (L_eff = (1 - e^{-alpha
+    L})/alpha) and the EDFA restores its amplitude, whatever the number of sub-steps.  A
+    wrong sub-step weight (e.g. the midpoint factor left out) moves the phase by ~20 % at
+    ten sub-steps per span."""
+    link = synth.link(1)
+    p0 = synth.dbm_to_w(4.0)
+    cw = np.full((2, 256), math.sqrt(p0) + 0j)
+    alpha = fiber.alpha_per_m(0.2)
+    leff = (1.0 - math.exp(-alpha * 80e3)) / alpha
+    gam = 1.3e-3 * 8.0 / 9.0
+    want = -gam * 2 * p0 * leff                    # joint intensity of both polarizations
+    for sps in (1, 10, 100):
+        u = olink.forward(cw, link, FS, steps_per_span=sps)
+        assert np.allclose(np.abs(u), math.sqrt(p0), rtol=1e-12)
+        assert np.allclose(np.angle(u), want, rtol=0, atol=1e-12)
+
+
+def test_ase_variance_closed_form():
+    """Section IV link (80 km spans, 0.2 dB/km, EDFA gain 16 dB, noise figure 5 dB) at
+    f_s = 56 GSa/s: n_sp h nu (G - 1) f_s with n_sp = F G / (2 (G - 1)) is F G h nu f_s / 2
+    per sample per polarization per amplifier, 4.517e-7 W (h nu at 1550 nm = 1.2816e-19 J),
+    so 4.5e-6 W after 10 spans and 1.8e-5 W after 40."""
+    link = synth.link(10)
+    var = olink.ase_variance(link, FS)
+    g = 10.0 ** 1.6                                 # 80 km x 0.2 dB/km = 16 dB
+    f = 10.0 ** 0.5
+    hnu = 6.62607015e-34 * 299792458.0 / 1550e-9
+    assert abs(hnu - 1.2816e-19) < 1e-23
+    assert abs(var - f * g * hnu * FS / 2.0) <= 1e-12 * var
+    assert abs(var - 4.517e-7) < 1e-9
+    assert abs(10 * var - 4.5e-6) < 0.05e-6
+    assert abs(40 * var - 1.8e-5) < 0.05e-5
+
+
+@pytest.mark.parametrize("n_spans,snr_db", [(10, 28.5), (40, 22.4)])
+def test_forward_ase_accumulates_to_closed_form(n_spans, snr_db):
+    """A zero signal through the forward simulator collects one amplifier's ASE per span
+    (the span loss and the EDFA gain cancel for the noise already present): mean power per
+    sample per polarization n_spans x 4.517e-7 W.  In the 28 GHz band of the 28 GBaud
+    signal (half of the 56 GHz sampled band) that is an SNR of 28.5 dB after 10 spans and
+    22.4 dB after 40 at 2 dBm per polarization."""
+    link = synth.link(n_spans)
+    n = 2 ** 16
+    u = olink.forward(np.zeros((2, n), complex), link, FS, steps_per_span=1, ase_seed=7 + n_spans)
+    p = np.mean(np.abs(u) ** 2)
+    want = n_spans * 4.517e-7
+    assert abs(p - want) < 0.015 * want            # 2^17 exponential samples: 0.28 % std
+    spec = np.abs(np.fft.fft(u, axis=-1)) ** 2 / n
+    f = np.fft.fftfreq(n, 1.0 / FS)
+    inband = np.sum(spec[:, np.abs(f) < 14e9]) / (2 * n)   # per sample per polarization
+    snr = 10.0 * math.log10(synth.dbm_to_w(2.0) / inband)
+    assert abs(snr - snr_db) < 0.1, snr
+
+
 
 def test_single_polarization_scalar_case():
     """One polarization (the scalar form Eq. 3 extends, P_k = |y_k|^2): (i) a CW field is
