@@ -245,6 +245,7 @@ def run_ours(args):
     single = single_pol_measure(torch, stream, fft_e) if not args.no_extras else None
     latency = latency_measure(torch, stream) if not args.no_extras else None
     fit = fit_measure(torch, stream, fft_e) if not args.no_extras else None
+    adam = fit_adam_measure(torch, stream) if not args.no_extras else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds, fft_e)
@@ -279,6 +280,7 @@ def run_ours(args):
             "single_pol": single,
             "latency": latency,
             "ls_fit": fit,
+            "adam_fit": adam,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -295,7 +297,7 @@ def batch_measure(torch, n_jobs: int, reps: int, stream):
     0-4 dBm, SSFM 5-20 steps / ESSFM 1-2 steps with 8-32 taps), block length autotuned
     per link length and method; one graph launch of the batch vs the same jobs launched
     one by one.  Returns aggregate vector samples/s of both."""
-    from paper_1507_00921_gb300 import Batch, Plan, autotune
+    from paper_1507_00921_gb300 import Batch, Plan, autotune, describe
     jobs = synth.batch_jobs(n_jobs, synth.BASE_SEED + 5)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(synth.BASE_SEED + 5)
@@ -311,13 +313,18 @@ def batch_measure(torch, n_jobs: int, reps: int, stream):
         n = jb["n_symbols"] * synth.SPS
         nc = jb["n_taps"]
         coeffs = essfm_coeffs(nc) if nc else None
+        choice = tuned[key]
         plan = None
-        for fft in sorted({tuned[key], 2048, 4096, 8192}):
-            if fft < tuned[key]:
+        for fft in sorted({choice.fft_size, 2048, 4096, 8192}):
+            if fft < choice.fft_size:
                 continue
             try:
+                # the tuned overlap margin above the rule, carried over to this job's own rule
+                o_min = describe(link, synth.SAMPLE_RATE, n, method=jb["method"], n_steps=jb["n_steps"],
+                                 n_taps=nc, fft_size=fft).overlap
+                o = o_min + (choice.overlap - choice.min_overlap if fft == choice.fft_size else 0)
                 plan = Plan(link, synth.SAMPLE_RATE, n, method=jb["method"], n_steps=jb["n_steps"], n_taps=nc,
-                            coeffs=coeffs, fft_size=fft)
+                            coeffs=coeffs, fft_size=fft, overlap=o if o < fft else 0)
                 break
             except Exception:
                 continue
@@ -354,7 +361,7 @@ def batch_measure(torch, n_jobs: int, reps: int, stream):
         p.close()
     return {"value": round(total / t_batch / 1e6, 1), "unit": UNIT, "jobs": n_jobs, "vector_samples": total,
             "one_by_one": round(total / t_seq / 1e6, 1), "speedup": round(t_seq / t_batch, 3), "status": status,
-            "block_lengths": {f"{k[0] * 80}km_{k[1]}": v for k, v in sorted(tuned.items())},
+            "block_length_overlap": {f"{k[0] * 80}km_{k[1]}": [v.fft_size, v.overlap] for k, v in sorted(tuned.items())},
             "launches": "1 CUDA graph launch (persistent kernel per block length)"}
 
 
@@ -478,6 +485,76 @@ def fit_measure(torch, stream, fft_size: int):
         dt = time.perf_counter() - t0
     return {"seconds": round(dt, 4), "updates": len(losses) - 1, "training_vector_samples": nw * n,
             "workload": f"3200 km ESSFM N_s=1 N_c={ESSFM_TAPS}, N={fft_size}, {nw} x 2^19 samples, 10 updates"}
+
+
+def gpu_channel(torch, x, n_spans: int, steps_per_span: int, seed: int, stream):
+    """Synthetic received waveforms for the training workload, made on the GPU: x (CUDA
+    complex64 [B, 2, n] at the launch power) through n_spans x 80 km of SMF, span by
+    span, each span as ``steps_per_span`` split steps of libdbp run on the mirrored link
+    (dispersion D -> -D and the per-step nonlinear strengths negated and in transmitter-
+    to-receiver order: the forward operators of Eqs. 1-2 in their lossless normalised
+    form), then the span's EDFA noise: circular Gaussian ASE of n_sp h nu (G - 1) f_s =
+    F G h nu f_s / 2 per sample per polarization (G the span loss, F = 5 dB)."""
+    from paper_1507_00921_gb300 import Plan, describe
+    fwd = synth.link(1, D_ps_per_nm_km=-synth.SMF["D_ps_per_nm_km"])
+    n = x.shape[-1]
+    info = describe(synth.link(1), synth.SAMPLE_RATE, n, method="ssfm", n_steps=steps_per_span, fft_size=1024)
+    g_fwd = -info.step_gamma_eff[::-1].copy()
+    gain = 10.0 ** (synth.SMF["alpha_db_per_km"] * synth.SMF["span_len_m"] / 1e3 / 10.0)
+    nf = 10.0 ** (synth.SMF["nf_db"] / 10.0)
+    hnu = 6.62607015e-34 * 299792458.0 / synth.SMF["lambda_m"]
+    sd = math.sqrt(nf * gain * hnu * synth.SAMPLE_RATE / 2.0 / 2.0)     # per real component
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    y = torch.empty_like(x)
+    with Plan(fwd, synth.SAMPLE_RATE, n, n_waveforms=x.shape[0], method="ssfm", n_steps=steps_per_span,
+              gamma_eff=g_fwd, fft_size=1024) as span:
+        for _ in range(n_spans):
+            span.run(x, y, stream=stream)
+            with torch.cuda.stream(stream):
+                noise = torch.randn(x.shape, dtype=torch.complex64, device="cuda", generator=gen)
+                x = y + noise * (sd * math.sqrt(2.0))
+        stream.synchronize()
+    return x
+
+
+def fit_adam_measure(torch, stream, n_iter: int = 200):
+    """Coefficient training at scale (Section IV footnote: MSE of the received symbols):
+    64 waveforms of 2^16 PM-QPSK symbols over 3200 km at 2 dBm, ESSFM N_c = 16 with
+    N_s in {1, 2, 4}, n_iter Adam iterations on the symbol MSE through libdbp's forward
+    and adjoint kernels (matched filter and gain in torch).  Reports the wall time, the
+    rate of forward + adjoint passes, and Q before (c = 1, 0, ..., 0, the SSFM) and after."""
+    from paper_1507_00921_gb300 import Plan, fit
+    nw, n_sym = 64, 2 ** 16
+    n = n_sym * synth.SPS
+    tx = np.empty((nw, 2, n), dtype=np.complex64)
+    sym = np.empty((nw, 2, n_sym), dtype=np.complex64)
+    for w in range(nw):
+        a, s_, _ = synth.pm_qpsk_waveform(n_sym, synth.BASE_SEED + 400 + w, LAUNCH_DBM)
+        tx[w], sym[w] = a, s_
+    x = gpu_channel(torch, torch.from_numpy(tx).cuda(), N_SPANS, 5, synth.BASE_SEED + 401, stream)
+    sd = torch.from_numpy(sym).cuda()
+    h_mf = fit.rrc_matched_response(n, synth.SPS, device=x.device)
+    out = {}
+    for ns in (1, 2, 4):
+        with Plan(synth.link(N_SPANS), synth.SAMPLE_RATE, n, n_waveforms=nw, method="essfm", n_steps=ns, n_taps=16,
+                  fft_size=8192) as plan:
+            with torch.cuda.stream(stream):
+                q0 = -10.0 * math.log10(float(fit.symbol_mse(plan.run(x, stream=stream), sd, h_mf, synth.SPS)))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                c, losses = fit.fit_adam(plan, x, sd, n_iter=n_iter, lr=2e-3, sps=synth.SPS)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                plan.set_coeffs(c)
+                q1 = -10.0 * math.log10(float(fit.symbol_mse(plan.run(x, stream=stream), sd, h_mf, synth.SPS)))
+        out[f"n_steps_{ns}"] = {"seconds": round(dt, 3), "iterations": n_iter,
+                                "fwd_adj_msps": round(nw * n * n_iter / dt / 1e6, 1),
+                                "q_db_start": round(q0, 3), "q_db_fitted": round(q1, 3)}
+    out["workload"] = ("3200 km, 2 dBm, 64 x 2^16 PM-QPSK symbols (2 sps), ESSFM N_c=16, N=8192, Adam lr 2e-3 on "
+                       "the symbol MSE; channel: libdbp on the mirrored link, 5 steps per span, ASE per span")
+    out["unit"] = "seconds (wall, whole fit)"
+    return out
 
 
 def fp32_pipe(value_msps: float, fft: int, overlap: int):

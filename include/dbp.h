@@ -233,23 +233,26 @@ int dbp_run_host(dbp_plan_t *plan, const void *in, void *out, dbp_stream_t strea
 
 /*
  * Backpropagation for callers that cannot allocate device memory (no counterpart in
- * the paper).  Some callers cannot call cudaMalloc: code that runs while a CUDA graph
- * is being built, a host that must keep to pre-reserved device memory, or an
- * application whose allocator must not be re-entered from a library.  This call takes
- * the same link / signal / step parameters as dbp_plan and the same DEVICE in/out
- * buffers as dbp_run, and computes exactly what dbp_plan + dbp_run compute, but it
- * allocates nothing: its tables (H_s, twiddles, filter taps) are rebuilt on every call
- * in one fixed scratch area of DBP_NOALLOC_SCRATCH_BYTES that lives in the library's
- * device image, so every GPU that loads the library holds it until the process exits.
+ * the paper).  Some callers cannot call cudaMalloc: a host that must keep to
+ * pre-reserved device memory, an application whose allocator must not be re-entered
+ * from a library, or a real-time receiver loop that cannot afford the device-wide
+ * synchronisation an allocation or a free may bring.  This call takes the same link /
+ * signal / step parameters as dbp_plan and the same DEVICE in/out buffers as dbp_run,
+ * and computes exactly what dbp_plan + dbp_run compute (bit for bit), but it allocates
+ * nothing: its tables (H_s, twiddles, filter taps) are rebuilt on every call in one
+ * fixed scratch area of DBP_NOALLOC_SCRATCH_BYTES that lives in the library's device
+ * image, so every GPU that loads the library holds it until the process exits.
  * Limits: at most DBP_NOALLOC_MAX_STEPS steps and tables that fit the scratch (for
  * example N = 8192 with equal step lengths, or up to 15 distinct step lengths at
- * N = 8192); beyond them it returns DBP_ERR_SCRATCH and does nothing.
- * All calls share the one scratch area, which keeps the last call's tables: calls that
- * overlap on the GPU (different streams, or different host threads) race on it and must
- * be serialized by the caller.  The first call on each device looks up the scratch
- * address with that device current; make that first call before any stream capture.
- * Asynchronous on `stream` (its small host-to-device copies read pageable host memory,
- * so it returns only after the host data has been staged).
+ * N = 8192); beyond them it returns DBP_ERR_SCRATCH and does nothing.  Two
+ * polarizations, FP32, fused scheme only (else DBP_ERR_UNSUPPORTED).
+ * All calls share the one scratch area, which keeps the last call's tables (every entry
+ * a call reads is rewritten by that call): calls that overlap on the GPU (different
+ * streams, or different host threads) race on it and must be serialized by the caller.
+ * The first call on each device looks up the scratch address with that device current
+ * (a one-time set-up); make that first call before any stream capture.  Asynchronous on
+ * `stream`: the host-side values of a call (taps, step lengths) travel as kernel
+ * arguments, no host memory is copied.
  */
 #define DBP_NOALLOC_SCRATCH_BYTES (1u << 20)
 #define DBP_NOALLOC_MAX_STEPS 64

@@ -1,13 +1,15 @@
 // dbp_run_noalloc: backpropagation without any device allocation.
 //
-// Some callers cannot allocate device memory at all: code running inside a CUDA graph
-// that is being built or replayed, a host that hands the library pre-reserved buffers
-// under a fixed memory budget, or an application whose allocator must not be re-entered
-// from a library.  This entry point serves them.  It needs no plan: every call computes
-// the step table on the host and builds the dispersion transfer functions, twiddles and
-// filter taps in one fixed scratch area, a file-scope __device__ array that every GPU
-// loading the library holds until the process exits, then runs the same fused DBP
-// kernel as dbp_run.  The caller still provides the input and output buffers.
+// Some callers cannot allocate device memory at all: a host that hands the library
+// pre-reserved buffers under a fixed memory budget, an application whose allocator must
+// not be re-entered from a library, or a real-time receiver loop that cannot afford the
+// device-wide synchronisation a cudaMalloc / cudaFree may bring.  This entry point serves
+// them.  It needs no plan: every call computes the step table on the host and builds the
+// dispersion transfer functions, twiddles and filter taps in one fixed scratch area, a
+// file-scope __device__ array that every GPU loading the library holds until the process
+// exits, then runs the same fused DBP kernel as dbp_run.  The caller still provides the
+// input and output buffers.  The host-side per-call values (filter taps, step lengths)
+// reach the device as kernel arguments, so no host memory is read by a copy.
 #include <mutex>
 
 #include "dbp_internal.cuh"
@@ -18,7 +20,9 @@ namespace dbp {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[DBP_NOALLOC_SCRATCH_BYTES];
 
 // Device address of g_noalloc_scratch per device, found once per device with that device
-// current (in host code the symbol itself is only a host-side stand-in).
+// current (in host code the symbol itself is only a host-side stand-in).  A
+// cudaDeviceReset of the device invalidates it; the library does not support calls after
+// one.
 static void *g_scratch_addr[64];
 static std::mutex g_scratch_mu;
 
@@ -37,6 +41,22 @@ static int scratch_for_current_device(void **out) {
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Host-computed values of one call, passed by value as the argument of the staging
+// kernel (17 KB, within the 32 KB kernel-parameter limit of sm_70 and later).
+constexpr int kNoallocTaps = DBP_NOALLOC_MAX_STEPS * (1 + 8 * ((DBP_MAX_TAPS + 7) / 8));
+struct NoallocArgs {
+    float taps[kNoallocTaps];            // gamma_eff_s * c_{s,i}, [n_steps][taps_stride]
+    double dz[DBP_NOALLOC_MAX_STEPS];    // step lengths of the H tables
+    int n_taps;                          // floats of taps in use
+    int n_dz;                            // entries of dz in use
+};
+static_assert(sizeof(NoallocArgs) <= 32000, "kernel parameter limit");
+
+__global__ void noalloc_stage_kernel(const NoallocArgs a, float *taps, double *dz) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_taps; i += gridDim.x * blockDim.x) taps[i] = a.taps[i];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_dz; i += gridDim.x * blockDim.x) dz[i] = a.dz[i];
+}
 
 }  // namespace dbp
 
@@ -82,21 +102,22 @@ extern "C" int dbp_run_noalloc(const dbp_link *link, const dbp_signal *signal, c
     unsigned char *sc = (unsigned char *)base;
     cudaStream_t st = (cudaStream_t)stream;
 
-    // taps gamma_eff_s * c_{s,i}, zero padded to whole 8-tap blocks (every entry written)
-    float taps[DBP_NOALLOC_MAX_STEPS * (1 + 8 * ((DBP_MAX_TAPS + 7) / 8))];
+    // taps gamma_eff_s * c_{s,i}, zero padded to whole 8-tap blocks (every entry written),
+    // and the step lengths, staged into the scratch by a kernel that takes them as its
+    // argument
+    NoallocArgs args;
+    args.n_taps = ns * taps_stride;
+    args.n_dz = n_tables;
     for (int s = 0; s < ns; ++s) {
         const float *c = steps->coeffs ? steps->coeffs + (steps->coeffs_per_step ? (size_t)s * (nt + 1) : 0) : nullptr;
         for (int i = 0; i < taps_stride; ++i) {
             double ci = 0.0;
             if (i <= nt) ci = c ? (double)c[i] : (i == 0 ? 1.0 : 0.0);
-            taps[s * taps_stride + i] = (float)(geff[s] * ci);
+            args.taps[s * taps_stride + i] = (float)(geff[s] * ci);
         }
     }
-    // pageable sources: each call returns once the host data has been staged
-    if (cudaMemcpyAsync(sc + off_taps, taps, sizeof(float) * (size_t)ns * taps_stride, cudaMemcpyHostToDevice, st) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(sc + off_dz, dz, sizeof(double) * (size_t)n_tables, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return DBP_ERR_CUDA;
+    for (int s = 0; s < n_tables; ++s) args.dz[s] = dz[s];
+    noalloc_stage_kernel<<<4, 256, 0, st>>>(args, (float *)(sc + off_taps), (double *)(sc + off_dz));
     float2 *H = (float2 *)(sc + off_h);
     build_h_kernel<<<dim3((N + 255) / 256, n_tables), 256, 0, st>>>(H, N, n0, n1, n2, info.beta2_s2_per_m,
                                                                      signal->sample_rate_hz,
@@ -114,7 +135,7 @@ extern "C" int dbp_run_noalloc(const dbp_link *link, const dbp_signal *signal, c
     P.n_tapblk = n_tapblk;
     P.taps_stride = taps_stride;
     P.h_shared = shared;
-    P.device = 0;
+    if (cudaGetDevice(&P.device) != cudaSuccess) return DBP_ERR_CUDA;
     P.d_H = H;
     P.d_taps = (float *)(sc + off_taps);
     P.d_twA = (float2 *)(sc + off_twa);

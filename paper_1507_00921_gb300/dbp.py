@@ -113,6 +113,7 @@ class Plan:
                                 C.byref(h))
         _lib.check(rc, "dbp_plan")
         self._h = h
+        self._coeffs = None if coeffs is None else np.array(coeffs, dtype=np.float32).ravel()
 
     # ------------------------------------------------------------------ helpers
     def _check_tensor(self, x, name):
@@ -232,6 +233,23 @@ class Plan:
         c = np.ascontiguousarray(coeffs, dtype=np.float32)
         rc = self._lib.dbp_set_coeffs(self._h, c.ctypes.data_as(C.POINTER(C.c_float)))
         _lib.check(rc, "dbp_set_coeffs")
+        self._coeffs = c.ravel().copy()
+
+    def apply_params(self, coeffs=None, gamma_eff=None, step_len_m=None):
+        """Makes the plan's coefficients, nonlinear strengths and step lengths equal to the
+        given host arrays (None keeps the current value), uploading only what changed."""
+        dz = None if step_len_m is None else np.asarray(step_len_m, dtype=np.float64).ravel()
+        ge = None if gamma_eff is None else np.asarray(gamma_eff, dtype=np.float64).ravel()
+        if dz is not None and np.array_equal(dz, self.info.step_dz):
+            dz = None
+        if ge is not None and np.array_equal(ge, self.info.step_gamma_eff):
+            ge = None
+        if dz is not None or ge is not None:
+            self.set_steps(dz, ge)
+        if coeffs is not None:
+            c = np.asarray(coeffs, dtype=np.float32).ravel()
+            if self._coeffs is None or not np.array_equal(c, self._coeffs):
+                self.set_coeffs(c)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -309,17 +327,30 @@ class Batch:
 def _autograd():
     import torch
 
+    def host(t, dtype):
+        return None if t is None else t.detach().to("cpu", dtype).numpy().copy()
+
     class DBPFunction(torch.autograd.Function):
-        """out = DBP(x; c) through libdbp; backward through dbp_grad (gradients with
-        respect to the waveform and the ESSFM coefficients)."""
+        """out = DBP(x; c, gamma_eff, dz) through libdbp; backward through dbp_grad.
+
+        ``DBPFunction.apply(x, coeffs, gamma_eff, step_len, plan)``: x the CUDA complex64
+        waveforms, coeffs the ESSFM coefficients (shape of the plan's coefficient table),
+        gamma_eff the per-step nonlinear strengths [n_steps] (1/W), step_len the per-step
+        lengths [n_steps] (m) that set H_s (Eq. 1); any of the three may be None to keep
+        the plan's current value.  The plan is brought to these values before the forward
+        kernel and again before the adjoint (dbp_set_coeffs / dbp_set_steps; the block
+        geometry and overlap stay those of the plan).  Returns the gradients of all four
+        tensor inputs (Eqs. 1-3 differentiated by the adjoint kernel)."""
 
         @staticmethod
-        def forward(ctx, x, coeffs, plan):
-            c = coeffs.detach().to("cpu", torch.float32).numpy()
-            plan.set_coeffs(c)
+        def forward(ctx, x, coeffs, gamma_eff, step_len, plan):
+            c = host(coeffs, torch.float32)
+            ge = host(gamma_eff, torch.float64)
+            dz = host(step_len, torch.float64)
+            plan.apply_params(c, ge, dz)
             ctx.plan = plan
-            ctx.coeffs = c
-            ctx.c_device, ctx.c_dtype = coeffs.device, coeffs.dtype
+            ctx.params = (c, ge, dz)
+            ctx.meta = [None if t is None else (t.device, t.dtype, t.shape) for t in (coeffs, gamma_eff, step_len)]
             ctx.save_for_backward(x)
             return plan.run(x.contiguous())
 
@@ -327,25 +358,39 @@ def _autograd():
         def backward(ctx, g_out):
             (x,) = ctx.saved_tensors
             plan = ctx.plan
-            plan.set_coeffs(ctx.coeffs)
-            g_in, d_c, _, _ = plan.grad(x, g_out.contiguous(), need_input=ctx.needs_input_grad[0])
-            return g_in, d_c.reshape(ctx.coeffs.shape).to(ctx.c_device, ctx.c_dtype), None
+            plan.apply_params(*ctx.params)
+            g_in, d_c, d_g, d_z = plan.grad(x, g_out.contiguous(), need_input=ctx.needs_input_grad[0])
+            grads = []
+            for g, meta, need in zip((d_c, d_g, d_z), ctx.meta, ctx.needs_input_grad[1:4]):
+                grads.append(g.reshape(meta[2]).to(meta[0], meta[1]) if (meta is not None and need) else None)
+            return (g_in, *grads, None)
 
     class DBP(torch.nn.Module):
-        """ESSFM/SSFM backpropagation with trainable coefficients (a torch module over a Plan)."""
+        """ESSFM/SSFM backpropagation as a torch module over a Plan, with the coefficients
+        c_{s,i}, the nonlinear strengths gamma_eff_s and the step lengths dz_s as
+        parameters (by default only the coefficients are trained: gamma_eff and c trade
+        off by a scale, and dz_s moves H_s)."""
 
-        def __init__(self, plan, coeffs=None):
+        def __init__(self, plan, coeffs=None, gamma_eff=None, step_len_m=None, train_coeffs=True,
+                     train_gamma_eff=False, train_step_len=False):
             super().__init__()
             nt = plan.info.n_taps
             shape = (plan.info.n_steps, nt + 1) if plan.coeffs_per_step else (nt + 1,)
             if coeffs is None:
                 coeffs = np.zeros(shape, dtype=np.float32)
                 coeffs[..., 0] = 1.0
+            ge = plan.info.step_gamma_eff if gamma_eff is None else gamma_eff
+            dz = plan.info.step_dz if step_len_m is None else step_len_m
             self.plan = plan
-            self.coeffs = torch.nn.Parameter(torch.tensor(np.array(coeffs, dtype=np.float32)).reshape(shape))
+            self.coeffs = torch.nn.Parameter(torch.tensor(np.array(coeffs, dtype=np.float32)).reshape(shape),
+                                             requires_grad=train_coeffs)
+            self.gamma_eff = torch.nn.Parameter(torch.tensor(np.array(ge, dtype=np.float64)),
+                                                requires_grad=train_gamma_eff)
+            self.step_len = torch.nn.Parameter(torch.tensor(np.array(dz, dtype=np.float64)),
+                                               requires_grad=train_step_len)
 
         def forward(self, x):
-            return DBPFunction.apply(x, self.coeffs, self.plan)
+            return DBPFunction.apply(x, self.coeffs, self.gamma_eff, self.step_len, self.plan)
 
     return DBPFunction, DBP
 

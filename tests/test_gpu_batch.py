@@ -1,6 +1,7 @@
-"""Batched uneven workloads through one CUDA-graph launch of persistent kernels: each
-job's output equals its own dbp_run; replays are identical; streaming jobs wait for
-their publish flag with a bounded spin and a never-published job ends in
+"""Batched uneven workloads through one CUDA-graph launch of persistent kernels: every
+job's output matches the FP64 oracle on sampled blocks (jobs of 2^12-2^18 symbols, the
+uneven-batch workload's range) and its own dbp_run; replays are identical; streaming jobs
+wait for their publish flag with a bounded spin and a never-published job ends in
 DBP_ERR_TIMEOUT without hanging."""
 import time
 
@@ -8,6 +9,8 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import dbp as odbp
+from oracle import fiber
 
 pytestmark = pytest.mark.gpu
 FS = synth.SAMPLE_RATE
@@ -34,10 +37,12 @@ def fft_for(spans, method, ns, nc):
     return 8192
 
 
-def make_jobs(torch, n_jobs, seed, max_log2=13):
+def make_jobs(torch, n_jobs, seed, max_log2=13, min_log2=9, specs=None):
+    """Plans, device inputs and zeroed outputs of a seeded uneven job list; `specs`
+    (if a list) receives each job's (link, plan keyword arguments)."""
     from paper_1507_00921_gb300 import Plan
     plans, ins, outs = [], [], []
-    for k, jb in enumerate(synth.batch_jobs(n_jobs, seed, 9, max_log2)):
+    for k, jb in enumerate(synth.batch_jobs(n_jobs, seed, min_log2, max_log2)):
         n = jb["n_symbols"] * synth.SPS
         nc = jb["n_taps"]
         coeffs = None
@@ -46,9 +51,11 @@ def make_jobs(torch, n_jobs, seed, max_log2=13):
             coeffs = (c / (c[0] + 2 * c[1:].sum())).astype(np.float32)
         nw = 1 + (k % 3)
         fft = fft_for(jb["n_spans"], jb["method"], jb["n_steps"], nc)
-        plans.append(Plan(synth.link(jb["n_spans"]), FS, n, n_waveforms=nw, method=jb["method"],
-                          n_steps=jb["n_steps"], n_taps=nc, coeffs=coeffs, fft_size=fft,
-                          boundary="zero" if k % 4 == 3 else "periodic"))
+        kw = dict(method=jb["method"], n_steps=jb["n_steps"], n_taps=nc, coeffs=coeffs, fft_size=fft,
+                  boundary="zero" if k % 4 == 3 else "periodic")
+        plans.append(Plan(synth.link(jb["n_spans"]), FS, n, n_waveforms=nw, **kw))
+        if specs is not None:
+            specs.append((synth.link(jb["n_spans"]), kw))
         x = synth.random_field(nw, n, synth.dbm_to_w(jb["launch_dbm"]), seed=jb["seed"]).astype(np.complex64)
         ins.append(torch.from_numpy(x).cuda())
         outs.append(torch.zeros_like(ins[-1]))
@@ -73,6 +80,47 @@ def test_batch_equals_individual_runs_and_replays(torch_cuda):
         assert torch.equal(o, f)
         err = (o - r).abs().max().item() / r.abs().max().item()
         assert err <= 1e-6, err
+    for p in plans:
+        p.close()
+
+
+def test_batch_matches_oracle_on_long_uneven_jobs(torch_cuda):
+    """The batch kernel (its own instantiation: per-item parameter loads, table twiddles)
+    against the FP64 oracle, on jobs of 2^12 to 2^18 symbols per polarization: the first,
+    the last and random blocks of the first and the last waveform of every job, at the
+    FP32 parity bar (relative RMS <= 1e-5, every sample within 1e-4 of the RMS)."""
+    torch = torch_cuda
+    from paper_1507_00921_gb300 import Batch
+    specs = []
+    plans, ins, outs = make_jobs(torch, 10, 2025, max_log2=18, min_log2=12, specs=specs)
+    assert max(x.shape[-1] for x in ins) > 2 ** 18.9 and min(x.shape[-1] for x in ins) < 2 ** 14
+    with Batch(plans, ins, outs) as batch:
+        batch.run()
+        assert batch.status() == 0
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for p, x, y, (link, kw) in zip(plans, ins, outs, specs):
+        info = p.info
+        xs, ys = x.cpu().numpy(), y.cpu().numpy()
+        c = kw["coeffs"]
+        cfg = fiber.make_config(link, FS, kw["n_steps"], kw["n_taps"], kw["fft_size"],
+                                coeffs=None if c is None else c.astype(np.float64), overlap=info.overlap,
+                                boundary=kw["boundary"], essfm=kw["method"] == "essfm")
+        n, v = xs.shape[-1], info.valid
+        for w in sorted({0, xs.shape[0] - 1}):
+            ids = np.unique(np.concatenate([[0, info.n_blocks - 1], rng.integers(0, info.n_blocks, 3)]))
+            ref = odbp.dbp_blocks(xs[w].astype(np.complex128), cfg, ids)
+            for j, b in enumerate(ids):
+                lo, hi = b * v, min((b + 1) * v, n)
+                got = ys[w][:, lo:hi].astype(np.complex128)
+                want = ref[j][:, : hi - lo]
+                rms = np.sqrt(np.mean(np.abs(want) ** 2))
+                rel_rms = np.sqrt(np.mean(np.abs(got - want) ** 2)) / rms
+                max_rel = np.max(np.abs(got - want)) / rms
+                worst = max(worst, rel_rms)
+                assert rel_rms <= 1e-5 and max_rel <= 1e-4, (kw, w, b, rel_rms, max_rel)
+    print(f"\nbatch vs oracle: worst relative RMS {worst:.2e}")
     for p in plans:
         p.close()
 

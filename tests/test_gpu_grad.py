@@ -157,3 +157,57 @@ def test_autograd_module(torch_cuda):
         _, d_c, _, _ = plan.grad(x, (2.0 / out.numel()) * (out - t))
     assert torch.allclose(g_c.cuda(), d_c, rtol=1e-5, atol=1e-9)
     assert g_x.shape == x.shape and torch.isfinite(torch.view_as_real(g_x)).all()
+
+
+def test_autograd_over_coeffs_gamma_and_step_lengths(torch_cuda):
+    """DBPFunction.apply(x, c, gamma_eff, dz, plan) (Eqs. 1-3 with all three parameter
+    sets as tensors): the forward output equals a plan built with those parameters, and
+    the four gradients of L = Re sum conj(v) DBP(x) equal the FP64 oracle's adjoint and,
+    for gamma_eff and dz, central finite differences of the oracle (h = 1e-4 relative)."""
+    torch = torch_cuda
+    from paper_1507_00921_gb300 import Plan
+    from paper_1507_00921_gb300.dbp import DBPFunction
+    link = synth.link(40)
+    n, nw, ns, nc = 7000, 1, 3, 8
+    c = coeffs_for(nc, ns, True)
+    dz = np.array([1.1e6, 0.9e6, 1.2e6])
+    x = synth.random_field(nw, n, synth.dbm_to_w(2.0), seed=71).astype(np.complex64)
+    v = synth.random_field(nw, n, 1.0, seed=72).astype(np.complex64)
+    kw = dict(method="essfm", n_steps=ns, n_taps=nc, fft_size=4096, coeffs_per_step=True)
+    with Plan(link, FS, n, n_waveforms=nw, **kw) as plan:
+        ge = plan.info.step_gamma_eff * np.array([0.9, 1.05, 1.2])
+        xd = torch.from_numpy(x).cuda().requires_grad_(True)
+        vd = torch.from_numpy(v).cuda()
+        ct = torch.tensor(c, requires_grad=True)
+        gt = torch.tensor(ge, requires_grad=True)
+        zt = torch.tensor(dz, requires_grad=True)
+        out = DBPFunction.apply(xd, ct, gt, zt, plan)
+        loss = (torch.conj(vd) * out).real.sum()
+        loss.backward()
+        ov = plan.info.overlap
+        with Plan(link, FS, n, n_waveforms=nw, coeffs=c.ravel(), step_len_m=dz, gamma_eff=ge, overlap=ov,
+                  **kw) as direct:
+            ref_out = direct.run(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+        assert torch.equal(out.detach(), ref_out)
+        g_x, g_c, g_g, g_z = xd.grad.cpu().numpy(), ct.grad.numpy(), gt.grad.numpy(), zt.grad.numpy()
+    cfg = fiber.make_config(link, FS, ns, nc, 4096, coeffs=c.astype(np.float64), overlap=ov, step_len_m=dz,
+                            gamma_eff=ge)
+    xx, vv = x[0].astype(np.complex128), v[0].astype(np.complex128)
+    r_x, r_c, r_g, r_z = oadj.dbp_vjp(xx, cfg, vv)
+    assert np.linalg.norm(g_x[0] - r_x) / np.linalg.norm(r_x) <= 1e-4
+    for got, ref in ((g_c, r_c), (g_g, r_g), (g_z, r_z)):
+        ok, e = close(got, ref)
+        assert ok, e
+
+    def loss_of(cf):
+        return float(np.real(np.sum(np.conj(vv) * odbp.dbp(xx, cf))))
+
+    for s in range(ns):
+        for attr, got in (("gamma_eff", g_g[s]), ("dz", g_z[s])):
+            h = 1e-4 * getattr(cfg, attr)[s]
+            a, b = copy.deepcopy(cfg), copy.deepcopy(cfg)
+            getattr(a, attr)[s] += h
+            getattr(b, attr)[s] -= h
+            fd = (loss_of(a) - loss_of(b)) / (2 * h)
+            assert abs(got - fd) <= TOL * max(abs(fd), 1e-6), (attr, s, got, fd)
