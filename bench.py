@@ -394,8 +394,20 @@ def precision_measure(torch, stream):
         with Plan(synth.link(10), synth.SAMPLE_RATE, n, n_waveforms=nw, method="essfm", n_steps=1, n_taps=16,
                   coeffs=essfm_coeffs(16), fft_size=1024, precision=prec, dft_block=na) as plan:
             t = time_plan(torch, lambda: plan.run(x, y, stream=stream), stream)
+            assert plan.status() == 0
         out[prec] = round(nw * n / t / 1e6, 1)
+    # the same split products on the warp-level mma.sync kernel, for comparison
+    os.environ["DBP_SPLIT_MMA_SYNC"] = "1"
+    try:
+        for prec in ("split_fp16", "split_bf16"):
+            with Plan(synth.link(10), synth.SAMPLE_RATE, n, n_waveforms=nw, method="essfm", n_steps=1, n_taps=16,
+                      coeffs=essfm_coeffs(16), fft_size=1024, precision=prec, dft_block=64) as plan:
+                t = time_plan(torch, lambda: plan.run(x, y, stream=stream), stream)
+            out[prec + "_mma_sync"] = round(nw * n / t / 1e6, 1)
+    finally:
+        os.environ.pop("DBP_SPLIT_MMA_SYNC", None)
     out["workload"] = "800 km ESSFM N_s=1 N_c=16, N=1024, N_a=64, 256 x 2^15 samples"
+    out["tensor_path"] = "split_* on tcgen05 (TMEM accumulators); split_*_mma_sync on warp-level mma.sync"
     out["unit"] = UNIT
     return out
 
@@ -523,7 +535,8 @@ def fit_adam_measure(torch, stream, n_iter: int = 200):
     64 waveforms of 2^16 PM-QPSK symbols over 3200 km at 2 dBm, ESSFM N_c = 16 with
     N_s in {1, 2, 4}, n_iter Adam iterations on the symbol MSE through libdbp's forward
     and adjoint kernels (matched filter and gain in torch).  Reports the wall time, the
-    rate of forward + adjoint passes, and Q before (c = 1, 0, ..., 0, the SSFM) and after."""
+    rate of forward + adjoint passes, and Q (10 log10 of 1 / symbol MSE) at the flat start
+    c_i = 1/(2 N_c + 1) and after the fit, with FFE and 20-step SSFM on the same waveforms."""
     from paper_1507_00921_gb300 import Plan, fit
     nw, n_sym = 64, 2 ** 16
     n = n_sym * synth.SPS
@@ -536,23 +549,33 @@ def fit_adam_measure(torch, stream, n_iter: int = 200):
     sd = torch.from_numpy(sym).cuda()
     h_mf = fit.rrc_matched_response(n, synth.SPS, device=x.device)
     out = {}
+
+    def q_of(plan):
+        with torch.cuda.stream(stream):
+            return -10.0 * math.log10(float(fit.symbol_mse(plan.run(x, stream=stream), sd, h_mf, synth.SPS)))
+
+    for name, kw in (("ffe", dict(method="ffe", n_steps=1)), ("ssfm20", dict(method="ssfm", n_steps=20))):
+        with Plan(synth.link(N_SPANS), synth.SAMPLE_RATE, n, n_waveforms=nw, fft_size=8192, **kw) as plan:
+            out[f"q_db_{name}"] = round(q_of(plan), 3)
+    nc = 16
+    c0 = np.full(nc + 1, 1.0 / (2 * nc + 1), dtype=np.float32)      # flat start, as in the equal-Q study
     for ns in (1, 2, 4):
-        with Plan(synth.link(N_SPANS), synth.SAMPLE_RATE, n, n_waveforms=nw, method="essfm", n_steps=ns, n_taps=16,
-                  fft_size=8192) as plan:
+        with Plan(synth.link(N_SPANS), synth.SAMPLE_RATE, n, n_waveforms=nw, method="essfm", n_steps=ns, n_taps=nc,
+                  coeffs=c0, fft_size=8192) as plan:
             with torch.cuda.stream(stream):
-                q0 = -10.0 * math.log10(float(fit.symbol_mse(plan.run(x, stream=stream), sd, h_mf, synth.SPS)))
+                q0 = q_of(plan)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                c, losses = fit.fit_adam(plan, x, sd, n_iter=n_iter, lr=2e-3, sps=synth.SPS)
+                c, losses = fit.fit_adam(plan, x, sd, coeffs0=c0, n_iter=n_iter, lr=1e-2, sps=synth.SPS)
                 torch.cuda.synchronize()
                 dt = time.perf_counter() - t0
                 plan.set_coeffs(c)
-                q1 = -10.0 * math.log10(float(fit.symbol_mse(plan.run(x, stream=stream), sd, h_mf, synth.SPS)))
+                q1 = q_of(plan)
         out[f"n_steps_{ns}"] = {"seconds": round(dt, 3), "iterations": n_iter,
                                 "fwd_adj_msps": round(nw * n * n_iter / dt / 1e6, 1),
                                 "q_db_start": round(q0, 3), "q_db_fitted": round(q1, 3)}
-    out["workload"] = ("3200 km, 2 dBm, 64 x 2^16 PM-QPSK symbols (2 sps), ESSFM N_c=16, N=8192, Adam lr 2e-3 on "
-                       "the symbol MSE; channel: libdbp on the mirrored link, 5 steps per span, ASE per span")
+    out["workload"] = ("3200 km, 2 dBm, 64 x 2^16 PM-QPSK symbols (2 sps), ESSFM N_c=16, N=8192, Adam lr 1e-2 from a "
+                       "flat filter on the symbol MSE (training Q); channel: libdbp on the mirrored link, 5 steps per span, ASE per span")
     out["unit"] = "seconds (wall, whole fit)"
     return out
 

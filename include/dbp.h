@@ -54,7 +54,10 @@ extern "C" {
                                    ceil(M_s) + 2 N_c, so short blocks suit long links  */
 #define DBP_FP32       0   /* FFT linear sub-step in FP32                               */
 #define DBP_SPLIT_BF16 1   /* linear sub-step as DFT-matrix GEMMs on the tensor cores,
-                              BF16 hi/lo split operands, FP32 accumulation              */
+                              BF16 hi/lo split operands, FP32 accumulation; dft_block
+                              64 with fft_size 1024 or 2048 runs on tcgen05 (5th-gen
+                              tensor cores, accumulators in tensor memory), the other
+                              sizes on warp-level mma.sync                              */
 #define DBP_SPLIT_FP16 2   /* the same with FP16 hi/lo split operands                  */
 
 /* Opaque stream handle: a cudaStream_t (NULL = legacy default stream). */
@@ -288,6 +291,13 @@ void dbp_batch_destroy(dbp_batch_t *batch);
 /* One-shot: create, run on `stream`, wait, destroy.  Returns the batch status. */
 int dbp_run_batch(dbp_plan_t *const *plans, const void *const *ins, void *const *outs, int n_jobs,
                   dbp_stream_t stream);
+
+/*
+ * Waits for the device, then returns DBP_ERR_TIMEOUT if a bounded wait inside one of
+ * the plan's tensor-core kernels (the split precisions' tcgen05 path) gave up since the
+ * last call (its outputs are then incomplete), else DBP_OK; clears the record.
+ */
+int dbp_plan_status(dbp_plan_t *plan);
 
 /* Frees the plan's device tables and scratch (synchronizes the device first). */
 void dbp_destroy(dbp_plan_t *plan);

@@ -82,6 +82,7 @@ _PROTOS = {
     "dbp_fit_coeffs": (C.c_int, [_P, _P, _P, C.c_longlong, C.c_int, C.c_double, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int), _P]),
     "dbp_run_noalloc": (C.c_int, [C.POINTER(dbp_link), C.POINTER(dbp_signal), C.POINTER(dbp_steps), _P, _P, _P]),
+    "dbp_plan_status": (C.c_int, [_P]),
     "dbp_destroy": (None, [_P]),
     "dbp_batch_create": (C.c_int, [C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.c_int, C.c_int, C.c_int,
                                    C.POINTER(_P)]),

@@ -109,6 +109,8 @@ struct PlanImpl {
     float2 *d_Hn = nullptr;   // split precisions: H_s / N in natural frequency order
     float2 *d_Wn = nullptr;   // split precisions: W_N^m
     uint32_t *d_F = nullptr;  // split precisions: DFT-matrix hi/lo tables
+    uint4 *d_Fu = nullptr;    // split precisions, N_a = 64: the same in the tcgen05 operand layout
+    int *d_err = nullptr;     // split precisions: bounded-wait status of the tensor-core kernel
     int device;
     // device tables
     float2 *d_H = nullptr;
@@ -149,6 +151,10 @@ int launch_gemm_fp16(const GemmParams &, int N, int NA, int n_wave, bool essfm, 
 int build_f_tables_bf16(uint32_t *F, int NA);
 int build_f_tables_fp16(uint32_t *F, int NA);
 int launch_gemm_plan(const PlanImpl &P, const void *in, void *out, int n_wave, cudaStream_t st);
+bool umma_supported(int N, int NA);
+int build_fu_tables(uint4 *Fu, int precision);
+int launch_umma(const GemmParams &q, const uint4 *Fu, int *err, int precision, int N, int n_wave, bool essfm,
+                cudaStream_t st, bool *used);
 int build_gemm_tables(PlanImpl &P);
 int launch_adj_512(const AdjParams &, int n_wave, bool essfm, cudaStream_t);
 int launch_adj_1024(const AdjParams &, int n_wave, bool essfm, cudaStream_t);

@@ -249,6 +249,8 @@ static void release(PlanImpl &P) {
     if (P.d_Hn) cudaFree(P.d_Hn);
     if (P.d_Wn) cudaFree(P.d_Wn);
     if (P.d_F) cudaFree(P.d_F);
+    if (P.d_Fu) cudaFree(P.d_Fu);
+    if (P.d_err) cudaFree(P.d_err);
     if (P.d_pp) cudaFree(P.d_pp);
     free(P.step_dz);
     free(P.step_geff);
@@ -567,6 +569,17 @@ int dbp_run_host(dbp_plan_t *plan, const void *in, void *out, dbp_stream_t strea
         if (cudaStreamWaitEvent(st, P.ev[1 + k], 0) != cudaSuccess) return DBP_ERR_CUDA;
     }
     return cudaStreamSynchronize(st) == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
+}
+
+int dbp_plan_status(dbp_plan_t *plan) {
+    if (!plan) return DBP_ERR_ARG;
+    PlanImpl &P = plan->impl;
+    if (cudaDeviceSynchronize() != cudaSuccess) return DBP_ERR_CUDA;
+    if (!P.d_err) return DBP_OK;
+    int e = 0;
+    if (cudaMemcpy(&e, P.d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DBP_ERR_CUDA;
+    if (e && cudaMemset(P.d_err, 0, sizeof(int)) != cudaSuccess) return DBP_ERR_CUDA;
+    return e;
 }
 
 void dbp_destroy(dbp_plan_t *plan) {

@@ -251,6 +251,11 @@ class Plan:
             if self._coeffs is None or not np.array_equal(c, self._coeffs):
                 self.set_coeffs(c)
 
+    def status(self):
+        """Waits for the device; 0, or DBP_ERR_TIMEOUT if a bounded wait of the plan's
+        tensor-core kernel gave up since the last call (the record is then cleared)."""
+        return self._lib.dbp_plan_status(self._h)
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.dbp_destroy(self._h)

@@ -34,10 +34,13 @@ def coeffs(nc):
     return (c / (c[0] + 2 * c[1:].sum())).astype(np.float32)
 
 
+# N_a = 64 with N = 1024 / 2048 runs on tcgen05 (tensor memory accumulators); the other
+# sizes on mma.sync
 CASES = [(prec, fft, na, spans, ns, nc)
          for prec in ("split_fp16", "split_bf16")
          for (fft, na, spans, ns, nc) in [(1024, 64, 10, 1, 16), (1024, 128, 10, 1, 16), (1024, 256, 10, 1, 16),
-                                          (2048, 128, 20, 2, 8), (4096, 256, 40, 1, 32), (2048, 64, 10, 3, 0)]]
+                                          (2048, 128, 20, 2, 8), (4096, 256, 40, 1, 32), (2048, 64, 10, 3, 0),
+                                          (2048, 64, 20, 2, 32), (1024, 64, 10, 4, 8)]]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}_N{c[1]}_NA{c[2]}_{c[3] * 80}km_ns{c[4]}_nc{c[5]}" for c in CASES])
@@ -54,6 +57,7 @@ def test_split_precision_against_oracle(torch_cuda, case):
               precision=prec, dft_block=na) as plan:
         got = plan.run(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.complex128)
         ov = plan.info.overlap
+        assert plan.status() == 0
     cfg = fiber.make_config(link, FS, ns, nc, fft, coeffs=None if c is None else c.astype(np.float64), overlap=ov,
                             essfm=nc > 0)
     ref = odbp.dbp(x.astype(np.complex128), cfg)
@@ -82,3 +86,24 @@ def test_split_precision_q_factor(torch_cuda):
     assert abs(q[("fp32", 0)] - q_ref) <= 0.05
     assert abs(q[("split_fp16", 64)] - q_ref) <= 0.05
     assert abs(q[("split_bf16", 64)] - q_ref) <= 0.05
+
+
+@pytest.mark.parametrize("prec", ["split_fp16", "split_bf16"])
+def test_tcgen05_and_mma_sync_paths_agree(torch_cuda, prec, monkeypatch):
+    """The tcgen05 kernel (N_a = 64) and the warp-level mma.sync kernel compute the same
+    split products in different orders: outputs agree to the split's own precision, over
+    several blocks per tile, ragged tails, zero boundary, one and two steps."""
+    torch = torch_cuda
+    from paper_1507_00921_gb300 import Plan
+    link = synth.link(10)
+    n = 5 * 1024 + 333
+    x = torch.from_numpy(synth.random_field(3, n, synth.dbm_to_w(3.0), seed=41).astype(np.complex64)).cuda()
+    outs = []
+    for legacy in ("0", "1"):
+        monkeypatch.setenv("DBP_SPLIT_MMA_SYNC", legacy)
+        with Plan(link, FS, n, n_waveforms=3, method="essfm", n_steps=2, n_taps=8, coeffs=coeffs(8),
+                  fft_size=1024, precision=prec, dft_block=64, boundary="zero") as plan:
+            outs.append(plan.run(x).cpu().numpy().astype(np.complex128))
+            assert plan.status() == 0
+    rel = np.linalg.norm(outs[0] - outs[1]) / np.linalg.norm(outs[1])
+    assert rel <= TOL[prec], rel
