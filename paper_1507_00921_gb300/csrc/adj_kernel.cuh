@@ -15,9 +15,13 @@
 // One CTA per block: a forward sweep stores each step's input (checkpoints); the reverse
 // sweep recomputes each step's linear sub-step from its checkpoint.  Per-block partial
 // sums of R_i and dL/ddz go to scratch and are reduced in a fixed order, so the result
-// is bitwise reproducible.
+// is bitwise reproducible.  At N = 4096 the kernel runs two CTAs per SM (128 registers a
+// thread) and keeps each thread's spectrum U and gradient g in tensor memory (tcgen05.st
+// / tcgen05.ld of its own TMEM lane, 256 columns per CTA) instead of global scratch;
+// y stays in global scratch.
 #pragma once
 #include "block_fft.cuh"
+#include "umma.cuh"
 
 namespace dbp {
 
@@ -123,8 +127,101 @@ struct MidAdjoint {
     }
 };
 
+// Tensor memory as per-thread scratch of the reverse sweep (N = 4096: 256 threads, two
+// per TMEM lane, 192 columns each): the thread's U (its 16 pass-3 positions), y and the
+// gradient g (its 16 pass-1 positions), 64 32-bit columns each, one float4 (both
+// polarizations) per position.  Every access is to the thread's own positions, so TMEM
+// replaces the round trip through global memory.
+__device__ __forceinline__ void tm_st16(uint32_t a, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};\n" ::"r"(a),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+// 16 consecutive columns (4 float4: 4 positions, both polarizations) of the thread's lane
+__device__ __forceinline__ void tm_store4(uint32_t a, float4 v0, float4 v1, float4 v2, float4 v3) {
+    const uint32_t r[16] = {__float_as_uint(v0.x), __float_as_uint(v0.y), __float_as_uint(v0.z), __float_as_uint(v0.w),
+                            __float_as_uint(v1.x), __float_as_uint(v1.y), __float_as_uint(v1.z), __float_as_uint(v1.w),
+                            __float_as_uint(v2.x), __float_as_uint(v2.y), __float_as_uint(v2.z), __float_as_uint(v2.w),
+                            __float_as_uint(v3.x), __float_as_uint(v3.y), __float_as_uint(v3.z), __float_as_uint(v3.w)};
+    tm_st16(a, r);
+}
+__device__ __forceinline__ void tm_load4(uint32_t a, float4 (&v)[4]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(a)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        v[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]), __uint_as_float(r[4 * j + 2]),
+                           __uint_as_float(r[4 * j + 3]));
+}
+
+// MidRecompute with U kept in TMEM (pass 3 with N0 = 16: positions base .. base + 15)
+template <int N>
+struct MidRecomputeTM {
+    const float2 *sH;
+    uint32_t ucol;
+    __device__ __forceinline__ void two(float2 (&u0)[16], float2 (&u1)[16], int base) {
+        MidMulH<N>{sH}.two(u0, u1, base);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            tm_store4(ucol + 16 * q, make_float4(u0[4 * q].x, u0[4 * q].y, u1[4 * q].x, u1[4 * q].y),
+                      make_float4(u0[4 * q + 1].x, u0[4 * q + 1].y, u1[4 * q + 1].x, u1[4 * q + 1].y),
+                      make_float4(u0[4 * q + 2].x, u0[4 * q + 2].y, u1[4 * q + 2].x, u1[4 * q + 2].y),
+                      make_float4(u0[4 * q + 3].x, u0[4 * q + 3].y, u1[4 * q + 3].x, u1[4 * q + 3].y));
+        tm_wait_st();
+    }
+};
+
+// MidAdjoint with U read from TMEM, four positions at a time
+template <int N>
+struct MidAdjointTM {
+    const float2 *sH;
+    uint32_t ucol;
+    float cphi;
+    float acc;
+    __device__ __forceinline__ void two(float2 (&u0)[16], float2 (&u1)[16], int base) {
+        MidAdjoint<N> m{sH, nullptr, cphi, 0.f};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float4 uu[4];
+            tm_load4(ucol + 16 * q, uu);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int j = 4 * q + jj;
+                acc = fmaf(m.phi_prime(base + j),
+                           MidAdjoint<N>::mimag(u0[j], make_float2(uu[jj].x, uu[jj].y)) +
+                               MidAdjoint<N>::mimag(u1[j], make_float2(uu[jj].z, uu[jj].w)),
+                           acc);
+            }
+        }
+        const float4 *hrow = reinterpret_cast<const float4 *>(sH + hphys<16>(base));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 h = hrow[j];
+            u0[2 * j] = cmulc(u0[2 * j], make_float2(h.x, h.y));
+            u1[2 * j] = cmulc(u1[2 * j], make_float2(h.x, h.y));
+            u0[2 * j + 1] = cmulc(u0[2 * j + 1], make_float2(h.z, h.w));
+            u1[2 * j + 1] = cmulc(u1[2 * j + 1], make_float2(h.z, h.w));
+        }
+    }
+};
+
 template <int N, bool ESSFM>
-__global__ void __launch_bounds__(Geo<N>::T, 1) dbp_adj_kernel(const AdjParams q) {
+__global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel(const AdjParams q) {
     using B = Blk<N>;
     using G = Geo<N>;
     const FwdParams &p = q.f;
@@ -132,6 +229,24 @@ __global__ void __launch_bounds__(Geo<N>::T, 1) dbp_adj_kernel(const AdjParams q
     B blk(smem_raw, threadIdx.x);
     float *red = reinterpret_cast<float *>(smem_raw + G::SMEM);
     const int t = threadIdx.x;
+    // N = 4096 (two CTAs per SM): U and g in tensor memory (256 columns per CTA: 128 per
+    // thread, two threads a lane), y in global scratch
+    constexpr bool TM = (N == 4096);
+    __shared__ uint32_t s_tmem;
+    uint32_t tcol = 0;
+    if constexpr (TM) {
+        static_assert(Geo<N>::T == 256 && B::C1 == 1 && B::N2 == 16 && G::N0 == 16, "thread-own scratch layout");
+        if (t < 32) {
+            tmem_alloc(&s_tmem, 256);
+            tmem_relinquish();
+        }
+        tmem_fence_before_sync();
+        __syncthreads();
+        tmem_fence_after_sync();
+        const int warp = t >> 5;
+        tcol = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 128u * (uint32_t)(warp >> 2);
+    }
+    const uint32_t tm_u = tcol, tm_g = tcol + 64;
     const int blkid = blockIdx.x;
     const int w = blkid / p.n_blocks;
     const int b = blkid - w * p.n_blocks;
@@ -154,19 +269,27 @@ __global__ void __launch_bounds__(Geo<N>::T, 1) dbp_adj_kernel(const AdjParams q
     {
         const int h = p.half_overlap;
         const long long obase = (long long)b * p.valid - h;
-#pragma unroll
-        for (int i = 0; i < B::C1; ++i)
-#pragma unroll
-            for (int j = 0; j < B::N2; ++j) {
-                const int e = blk.pos1(i, j);
-                const long long g = obase + e;
-                float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (e >= h && e < h + p.valid && g < n) {
-                    const float2 g0 = __ldg(gout + g), g1 = __ldg(gout + n + g);
-                    val = make_float4(g0.x, g0.y, g1.x, g1.y);
-                }
-                gb[e] = val;
+        auto gval = [&](int i, int j) {
+            const int e = blk.pos1(i, j);
+            const long long g = obase + e;
+            float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e >= h && e < h + p.valid && g < n) {
+                const float2 g0 = __ldg(gout + g), g1 = __ldg(gout + n + g);
+                val = make_float4(g0.x, g0.y, g1.x, g1.y);
             }
+            return val;
+        };
+        if constexpr (TM) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                tm_store4(tm_g + 16 * q, gval(0, 4 * q), gval(0, 4 * q + 1), gval(0, 4 * q + 2), gval(0, 4 * q + 3));
+            tm_wait_st();
+        } else {
+#pragma unroll
+            for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+                for (int j = 0; j < B::N2; ++j) gb[blk.pos1(i, j)] = gval(i, j);
+        }
     }
     __syncthreads();
 
@@ -230,13 +353,18 @@ __global__ void __launch_bounds__(Geo<N>::T, 1) dbp_adj_kernel(const AdjParams q
             blk.prefetch_h(p.H + p.h_stride * s);
         }
         // recompute the linear sub-step, keeping U = H' X
-        MidRecompute<N> rec{blk.sH, ub};
         blk.pass1_fwd(v);
         __syncthreads();
         blk.template pass2<false>();
         cp_async_wait_all();
         __syncthreads();
-        blk.pass3(rec);
+        if constexpr (TM) {
+            MidRecomputeTM<N> rec{blk.sH, tm_u};
+            blk.pass3(rec);
+        } else {
+            MidRecompute<N> rec{blk.sH, ub};
+            blk.pass3(rec);
+        }
         __syncthreads();
         blk.template pass2<true>();
         __syncthreads();
@@ -252,18 +380,27 @@ __global__ void __launch_bounds__(Geo<N>::T, 1) dbp_adj_kernel(const AdjParams q
 #pragma unroll
             for (int i = 0; i < B::C1; ++i)
 #pragma unroll
-                for (int j = 0; j < B::N2; ++j) {
-                    const int e = blk.pos1(i, j);
-                    const float2 ex = expj(sT[pphys(e)]);
-                    const float2 y0 = v[0][i][j], y1 = v[1][i][j];
-                    const float2 z0 = cmul(y0, ex), z1 = cmul(y1, ex);
-                    const float4 g = gb[e];
-                    const float2 g0 = make_float2(g.x, g.y), g1 = make_float2(g.z, g.w);
-                    sS[pphys(e)] = MidAdjoint<N>::mimag(g0, z0) + MidAdjoint<N>::mimag(g1, z1);
-                    const float2 d0 = cmulc(g0, ex), d1 = cmulc(g1, ex);
-                    gb[e] = make_float4(d0.x, d0.y, d1.x, d1.y);
-                    yb[e] = make_float4(y0.x, y0.y, y1.x, y1.y);
+                for (int q = 0; q < B::N2 / 4; ++q) {
+                    float4 gq[4];
+                    if constexpr (TM) tm_load4(tm_g + 16 * q, gq);
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = 4 * q + jj;
+                        const int e = blk.pos1(i, j);
+                        const float2 ex = expj(sT[pphys(e)]);
+                        const float2 y0 = v[0][i][j], y1 = v[1][i][j];
+                        const float2 z0 = cmul(y0, ex), z1 = cmul(y1, ex);
+                        const float4 g = TM ? gq[jj] : gb[e];
+                        const float2 g0 = make_float2(g.x, g.y), g1 = make_float2(g.z, g.w);
+                        sS[pphys(e)] = MidAdjoint<N>::mimag(g0, z0) + MidAdjoint<N>::mimag(g1, z1);
+                        const float2 d0 = cmulc(g0, ex), d1 = cmulc(g1, ex);
+                        gq[jj] = make_float4(d0.x, d0.y, d1.x, d1.y);
+                        if constexpr (!TM) gb[e] = gq[jj];
+                        yb[e] = make_float4(y0.x, y0.y, y1.x, y1.y);
+                    }
+                    if constexpr (TM) tm_store4(tm_g + 16 * q, gq[0], gq[1], gq[2], gq[3]);
                 }
+            if constexpr (TM) tm_wait_st();
             __syncthreads();
             // correlations R_i = sum_k s_k S_{k,i}, then dL/dP = filter(s) into farr(1)
             {
@@ -308,16 +445,33 @@ __global__ void __launch_bounds__(Geo<N>::T, 1) dbp_adj_kernel(const AdjParams q
             }
             __syncthreads();
             const float *sD = blk.farr(1);
+            if constexpr (TM) {
 #pragma unroll
-            for (int i = 0; i < B::C1; ++i)
+                for (int q = 0; q < B::N2 / 4; ++q) {
+                    float4 gq[4];
+                    tm_load4(tm_g + 16 * q, gq);
 #pragma unroll
-                for (int j = 0; j < B::N2; ++j) {
-                    const int e = blk.pos1(i, j);
-                    const float dp2 = 2.f * sD[pphys(e)];
-                    const float4 g = gb[e], y = yb[e];
-                    v[0][i][j] = make_float2(fmaf(dp2, y.x, g.x), fmaf(dp2, y.y, g.y));
-                    v[1][i][j] = make_float2(fmaf(dp2, y.z, g.z), fmaf(dp2, y.w, g.w));
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = 4 * q + jj;
+                        const int e = blk.pos1(0, j);
+                        const float dp2 = 2.f * sD[pphys(e)];
+                        const float4 g = gq[jj], y = yb[e];
+                        v[0][0][j] = make_float2(fmaf(dp2, y.x, g.x), fmaf(dp2, y.y, g.y));
+                        v[1][0][j] = make_float2(fmaf(dp2, y.z, g.z), fmaf(dp2, y.w, g.w));
+                    }
                 }
+            } else {
+#pragma unroll
+                for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+                    for (int j = 0; j < B::N2; ++j) {
+                        const int e = blk.pos1(i, j);
+                        const float dp2 = 2.f * sD[pphys(e)];
+                        const float4 g = gb[e], y = yb[e];
+                        v[0][i][j] = make_float2(fmaf(dp2, y.x, g.x), fmaf(dp2, y.y, g.y));
+                        v[1][i][j] = make_float2(fmaf(dp2, y.z, g.z), fmaf(dp2, y.w, g.w));
+                    }
+            }
         } else {
             const float a0 = __ldg(a);
             float r0[1] = {0.f};
@@ -326,11 +480,13 @@ __global__ void __launch_bounds__(Geo<N>::T, 1) dbp_adj_kernel(const AdjParams q
 #pragma unroll
                 for (int j = 0; j < B::N2; ++j) {
                     const int e = blk.pos1(i, j);
+                    float4 gq[4];
+                    if (TM && (j & 3) == 0) tm_load4(tm_g + 4 * j, gq);
                     const float2 y0 = v[0][i][j], y1 = v[1][i][j];
                     const float pk = joint_intensity(y0, y1);
                     const float2 ex = expj(a0 * pk);
                     const float2 z0 = cmul(y0, ex), z1 = cmul(y1, ex);
-                    const float4 g = gb[e];
+                    const float4 g = TM ? gq[j & 3] : gb[e];
                     const float2 g0 = make_float2(g.x, g.y), g1 = make_float2(g.z, g.w);
                     const float sk = MidAdjoint<N>::mimag(g0, z0) + MidAdjoint<N>::mimag(g1, z1);
                     r0[0] = fmaf(sk, pk, r0[0]);
@@ -343,25 +499,46 @@ __global__ void __launch_bounds__(Geo<N>::T, 1) dbp_adj_kernel(const AdjParams q
         }
         // linear adjoint: x conj(H'), with the step-length gradient
         __syncthreads();
-        MidAdjoint<N> adj{blk.sH, ub, q.cphi, 0.f};
         blk.pass1_fwd(v);
         __syncthreads();
         blk.template pass2<false>();
         __syncthreads();
-        blk.pass3(adj);
+        float dzacc;
+        if constexpr (TM) {
+            MidAdjointTM<N> adj{blk.sH, tm_u, q.cphi, 0.f};
+            blk.pass3(adj);
+            dzacc = adj.acc;
+        } else {
+            MidAdjoint<N> adj{blk.sH, ub, q.cphi, 0.f};
+            blk.pass3(adj);
+            dzacc = adj.acc;
+        }
         __syncthreads();
         blk.template pass2<true>();
         __syncthreads();
         blk.pass1_inv(v);   // v = g_x
         {
-            float dz[1] = {adj.acc};
+            float dz[1] = {dzacc};
             block_sum<N, 1>(dz, red, part + ns * q.nr + s, t);
         }
+        if (TM && s > 0) {   // the next (earlier) step's output gradient stays in TMEM
+            auto gx = [&](int j) { return make_float4(v[0][0][j].x, v[0][0][j].y, v[1][0][j].x, v[1][0][j].y); };
 #pragma unroll
-        for (int i = 0; i < B::C1; ++i)
+            for (int q = 0; q < 4; ++q) tm_store4(tm_g + 16 * q, gx(4 * q), gx(4 * q + 1), gx(4 * q + 2), gx(4 * q + 3));
+            tm_wait_st();
+        } else {
 #pragma unroll
-            for (int j = 0; j < B::N2; ++j)
-                gb[blk.pos1(i, j)] = make_float4(v[0][i][j].x, v[0][i][j].y, v[1][i][j].x, v[1][i][j].y);
+            for (int i = 0; i < B::C1; ++i)
+#pragma unroll
+                for (int j = 0; j < B::N2; ++j)
+                    gb[blk.pos1(i, j)] = make_float4(v[0][i][j].x, v[0][i][j].y, v[1][i][j].x, v[1][i][j].y);
+        }
+    }
+    if constexpr (TM) {   // every tcgen05 access has been waited for; free the columns
+        tmem_fence_before_sync();
+        __syncthreads();
+        tmem_fence_after_sync();
+        if (t < 32) tmem_dealloc(s_tmem, 256);
     }
 }
 
