@@ -776,6 +776,39 @@ def run_sweep(args):
                       "peak_gbs": peak, "peak_kind": peak_kind, "best": summary}), flush=True)
 
 
+def run_case(name: str):
+    """One small fixed workload per kernel, run a few times and checked, for ncu captures
+    (not a benchmark): ``split`` the tcgen05 split-FP16 DFT-GEMM kernel (800 km ESSFM N_s=1
+    N_c=16, N=1024, N_a=64, 64 x 2^15 samples), ``adjoint`` the reverse-mode kernel (3200 km
+    ESSFM N_s=1 N_c=16, N=4096, 64 x 2^17 samples), ``forward`` the headline kernel (3200 km
+    ESSFM N_s=1 N_c=32, N=8192, 16 x 2^19 samples)."""
+    import torch
+    from paper_1507_00921_gb300 import Plan
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.BASE_SEED + 9)
+    amp = math.sqrt(synth.dbm_to_w(LAUNCH_DBM))
+    if name == "split":
+        n, nw, kw, spans = 2 ** 15, 64, dict(method="essfm", n_steps=1, n_taps=16, coeffs=essfm_coeffs(16),
+                                             fft_size=1024, precision="split_fp16", dft_block=64), 10
+    elif name == "adjoint":
+        n, nw, kw, spans = 2 ** 17, 64, dict(method="essfm", n_steps=1, n_taps=16, coeffs=essfm_coeffs(16),
+                                             fft_size=4096), N_SPANS
+    else:
+        n, nw, kw, spans = N_SAMPLES, 16, dict(method="essfm", n_steps=1, n_taps=ESSFM_TAPS,
+                                               coeffs=essfm_coeffs(ESSFM_TAPS), fft_size=8192), N_SPANS
+    x = torch.randn((nw, 2, n), dtype=torch.complex64, device="cuda", generator=gen) * amp
+    with Plan(synth.link(spans), synth.SAMPLE_RATE, n, n_waveforms=nw, **kw) as plan:
+        for _ in range(3):
+            if name == "adjoint":
+                plan.grad(x, x)
+            else:
+                plan.run(x)
+        torch.cuda.synchronize()
+        status = plan.status()
+    assert status == 0, status
+    print(json.dumps({"case": name, "n_waveforms": nw, "samples_per_waveform": n, "status": status}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -789,7 +822,12 @@ def main():
     ap.add_argument("--batch-jobs", type=int, default=256, help="uneven batched workload size (0: skip)")
     ap.add_argument("--no-extras", action="store_true", help="skip the precision-variant and adjoint lines")
     ap.add_argument("--sweep", action="store_true", help="3200 km method / steps / taps / block-length sweep")
+    ap.add_argument("--case", choices=["split", "adjoint", "forward"],
+                    help="run one small fixed workload of that kernel (for profiling) and exit")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
