@@ -295,8 +295,8 @@ def run_ours(args):
 def batch_measure(torch, n_jobs: int, reps: int, stream):
     """Uneven workload: n_jobs waveforms (log-uniform 2^12..2^18 symbols, 800-3200 km,
     0-4 dBm, SSFM 5-20 steps / ESSFM 1-2 steps with 8-32 taps), block length autotuned
-    per link length and method; one graph launch of the batch vs the same jobs launched
-    one by one.  Returns aggregate vector samples/s of both."""
+    per link length and method; one graph launch of the batch (one persistent kernel over
+    the blocks of every length) vs the same jobs launched one by one.  Returns aggregate vector samples/s of both."""
     from paper_1507_00921_gb300 import Batch, Plan, autotune, describe
     jobs = synth.batch_jobs(n_jobs, synth.BASE_SEED + 5)
     gen = torch.Generator(device="cuda")
@@ -362,7 +362,7 @@ def batch_measure(torch, n_jobs: int, reps: int, stream):
     return {"value": round(total / t_batch / 1e6, 1), "unit": UNIT, "jobs": n_jobs, "vector_samples": total,
             "one_by_one": round(total / t_seq / 1e6, 1), "speedup": round(t_seq / t_batch, 3), "status": status,
             "block_length_overlap": {f"{k[0] * 80}km_{k[1]}": [v.fft_size, v.overlap] for k, v in sorted(tuned.items())},
-            "launches": "1 CUDA graph launch (persistent kernel per block length)"}
+            "launches": "1 CUDA graph launch of one persistent kernel (all block lengths)"}
 
 
 def time_plan(torch, fn, stream, reps=10):

@@ -264,11 +264,12 @@ int dbp_run_noalloc(const dbp_link *link, const dbp_signal *signal, const dbp_st
 
 /*
  * Batched launch of many jobs of uneven size (plans of any block length, link length,
- * step count and filter length, each with its own DEVICE in/out buffers).  A batch is
- * built once and replayed: jobs are grouped by block length, each group is served by a
- * persistent kernel whose CTAs pop (job, waveform, block) items from a device counter,
- * and the group kernels are captured as parallel branches of one CUDA graph.  Plans and
- * buffers must stay alive and unchanged in place while the batch exists.
+ * step count and filter length, each with its own DEVICE in/out buffers; two
+ * polarizations, FP32, fused scheme).  A batch is built once and replayed: the blocks
+ * of all jobs are cut into work units (several blocks side by side for the shorter
+ * block lengths), one persistent kernel pops the units of every block length from one
+ * device counter, longest blocks first, and that kernel is captured in a CUDA graph.
+ * Plans and buffers must stay alive and unchanged in place while the batch exists.
  * flags: 0, or DBP_BATCH_STREAMING: every job's input is read only after
  * dbp_batch_publish(job) (a producer may fill inputs while the batch runs).  A job that
  * is not published within timeout_us microseconds (0 = 1 s) is skipped and the batch

@@ -1,11 +1,12 @@
 // Batched launch of many DBP jobs of uneven size in one CUDA graph.
 //
 // A batch is built once from a list of plans and their device buffers.  Jobs are
-// grouped by block length N; each group is served by one persistent kernel whose CTAs
-// pop (job, waveform, block) items from a device counter, so short and long waveforms,
-// different link lengths, step counts and filter lengths share the GPU without one
-// launch per job.  The group kernels run on parallel branches of one captured CUDA
-// graph; dbp_batch_run replays it with a single graph launch.
+// grouped by block length N and the blocks of every group are cut into work units of as
+// many blocks as one 512-thread CTA runs side by side at that length (batch_kernel.cu);
+// one persistent kernel pops the units of all groups from one device counter, longest
+// blocks first, so short and long waveforms, different link lengths, step counts and
+// filter lengths share the SMs dynamically without one launch per job.  The kernel is
+// captured in a CUDA graph; dbp_batch_run replays it with a single graph launch.
 //
 // Streaming: with DBP_BATCH_STREAMING every job waits (bounded) for dbp_batch_publish
 // before its input is read, so a producer can fill input buffers while the batch is
@@ -21,71 +22,37 @@
 
 namespace dbp {
 
-struct BatchGroupHost {
-    int N;
-    int n_jobs;
-    long long n_items;
-    BatchJob *d_jobs;        // device
-    int grid;
-    cudaStream_t stream;
-    cudaEvent_t done;
-};
-
 struct BatchImpl {
     int device = 0;
     int n_jobs = 0;
     int streaming = 0;
     int max_spins = 0;
-    std::vector<BatchGroupHost> groups;
-    std::vector<int> job_group, job_index;    // per input job
-    BatchJob *d_jobs = nullptr;               // all jobs, grouped
+    int grid = 0;
+    long long n_units = 0;
+    BatchJob *d_jobs = nullptr;               // all jobs, grouped by block length
+    BatchGroupDev *d_groups = nullptr;
+    BatchUnit *d_units = nullptr;
     int *d_ready = nullptr;                   // [n_jobs] publish flags (input order)
-    unsigned long long *d_counters = nullptr; // [groups]
+    unsigned long long *d_counter = nullptr;  // unit counter
     int *d_error = nullptr;
     int *h_one = nullptr;                     // pinned constant 1 for publishing
     cudaStream_t cap = nullptr;
-    cudaEvent_t fork = nullptr, reset_done = nullptr;
+    cudaEvent_t reset_done = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
-
-static int prepare_group(BatchGroupHost &g) {
-    switch (g.N) {
-        case 512: return prepare_batch_512(g.n_items, &g.grid);
-        case 1024: return prepare_batch_1024(g.n_items, &g.grid);
-        case 2048: return prepare_batch_2048(g.n_items, &g.grid);
-        case 4096: return prepare_batch_4096(g.n_items, &g.grid);
-        case 8192: return prepare_batch_8192(g.n_items, &g.grid);
-        default: return DBP_ERR_INFEASIBLE;
-    }
-}
-
-static int launch_group(const BatchGroupHost &g, unsigned long long *counter, int *error, int max_spins,
-                        cudaStream_t st) {
-    switch (g.N) {
-        case 512: return launch_batch_512(g.d_jobs, g.n_jobs, g.n_items, counter, error, max_spins, g.grid, st);
-        case 1024: return launch_batch_1024(g.d_jobs, g.n_jobs, g.n_items, counter, error, max_spins, g.grid, st);
-        case 2048: return launch_batch_2048(g.d_jobs, g.n_jobs, g.n_items, counter, error, max_spins, g.grid, st);
-        case 4096: return launch_batch_4096(g.d_jobs, g.n_jobs, g.n_items, counter, error, max_spins, g.grid, st);
-        case 8192: return launch_batch_8192(g.d_jobs, g.n_jobs, g.n_items, counter, error, max_spins, g.grid, st);
-        default: return DBP_ERR_INFEASIBLE;
-    }
-}
 
 static void batch_release(BatchImpl *B) {
     if (!B) return;
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
-    for (auto &g : B->groups) {
-        if (g.stream) cudaStreamDestroy(g.stream);
-        if (g.done) cudaEventDestroy(g.done);
-    }
     if (B->cap) cudaStreamDestroy(B->cap);
-    if (B->fork) cudaEventDestroy(B->fork);
     if (B->reset_done) cudaEventDestroy(B->reset_done);
     if (B->d_jobs) cudaFree(B->d_jobs);
+    if (B->d_groups) cudaFree(B->d_groups);
+    if (B->d_units) cudaFree(B->d_units);
     if (B->d_ready) cudaFree(B->d_ready);
-    if (B->d_counters) cudaFree(B->d_counters);
+    if (B->d_counter) cudaFree(B->d_counter);
     if (B->d_error) cudaFree(B->d_error);
     if (B->h_one) cudaFreeHost(B->h_one);
     delete B;
@@ -121,11 +88,10 @@ extern "C" int dbp_batch_create(dbp_plan_t *const *plans, const void *const *ins
     B->n_jobs = n_jobs;
     B->streaming = (flags & DBP_BATCH_STREAMING) ? 1 : 0;
     B->max_spins = timeout_us > 0 ? timeout_us : 1000000;   // polls of ~1 us
-    B->job_group.assign(n_jobs, -1);
-    B->job_index.assign(n_jobs, -1);
     const int sizes[5] = {8192, 4096, 2048, 1024, 512};
     int rc = dev_alloc((void **)&B->d_ready, sizeof(int) * n_jobs);
     if (!rc) rc = dev_alloc((void **)&B->d_error, sizeof(int));
+    if (!rc) rc = dev_alloc((void **)&B->d_counter, sizeof(unsigned long long));
     if (!rc) rc = dev_alloc((void **)&B->d_jobs, sizeof(BatchJob) * n_jobs);
     if (!rc && cudaMallocHost((void **)&B->h_one, sizeof(int)) != cudaSuccess) rc = DBP_ERR_ALLOC;
     if (rc) {
@@ -133,61 +99,65 @@ extern "C" int dbp_batch_create(dbp_plan_t *const *plans, const void *const *ins
         return rc;
     }
     *B->h_one = 1;
+    // jobs grouped by block length (longest first), units of up to K(N) blocks per group
     std::vector<BatchJob> host;
+    std::vector<BatchGroupDev> groups;
+    std::vector<BatchUnit> units;
     host.reserve(n_jobs);
     for (int si = 0; si < 5; ++si) {
-        BatchGroupHost g{};
-        g.N = sizes[si];
+        const int N = sizes[si];
         const size_t first = host.size();
         long long items = 0;
         for (int j = 0; j < n_jobs; ++j) {
             const PlanImpl &P = plans[j]->impl;
-            if (P.info.fft_size != g.N) continue;
+            if (P.info.fft_size != N) continue;
             BatchJob J;
             memset(&J, 0, sizeof(J));
             fill_fwd_params(P, J.p);
             J.p.in = (const float2 *)ins[j];
             J.p.out = (float2 *)outs[j];
+            J.p.bulk_store = 0;
             J.item0 = items;
             J.essfm = P.method == DBP_ESSFM;
             J.ready = B->d_ready + j;
             items += (long long)P.info.n_blocks * P.signal.n_waveforms;
-            B->job_group[j] = (int)B->groups.size();
-            B->job_index[j] = (int)(host.size() - first);
             host.push_back(J);
         }
         if (host.size() == first) continue;
+        BatchGroupDev g;
+        g.jobs = B->d_jobs + first;
         g.n_jobs = (int)(host.size() - first);
-        g.n_items = items;
-        g.d_jobs = B->d_jobs + first;
-        B->groups.push_back(g);
+        g.N = N;
+        const int k = batch_unit_blocks(N);
+        for (long long i = 0; i < items; i += k) {
+            BatchUnit u;
+            u.item0 = i;
+            u.group = (int)groups.size();
+            u.count = (int)(items - i < k ? items - i : k);
+            units.push_back(u);
+        }
+        groups.push_back(g);
     }
-    if (cudaMemcpy(B->d_jobs, host.data(), sizeof(BatchJob) * host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    B->n_units = (long long)units.size();
+    if (!rc) rc = dev_alloc((void **)&B->d_groups, sizeof(BatchGroupDev) * groups.size());
+    if (!rc) rc = dev_alloc((void **)&B->d_units, sizeof(BatchUnit) * units.size());
+    if (!rc && (cudaMemcpy(B->d_jobs, host.data(), sizeof(BatchJob) * host.size(), cudaMemcpyHostToDevice) !=
+                    cudaSuccess ||
+                cudaMemcpy(B->d_groups, groups.data(), sizeof(BatchGroupDev) * groups.size(),
+                           cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(B->d_units, units.data(), sizeof(BatchUnit) * units.size(), cudaMemcpyHostToDevice) !=
+                    cudaSuccess))
         rc = DBP_ERR_CUDA;
-    if (!rc) rc = dev_alloc((void **)&B->d_counters, sizeof(unsigned long long) * B->groups.size());
     if (!rc && (cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&B->reset_done, cudaEventDisableTiming) != cudaSuccess))
         rc = DBP_ERR_CUDA;
-    for (auto &g : B->groups) {
-        if (rc) break;
-        rc = prepare_group(g);
-        if (rc) break;
-        if (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess)
-            rc = DBP_ERR_CUDA;
-    }
-    // capture: fork one branch per block-length group, join
+    if (!rc) rc = prepare_batch_unified(&B->grid);
+    if (!rc && B->n_units < B->grid) B->grid = (int)(B->n_units > 0 ? B->n_units : 1);
+    // capture the one kernel launch
     if (!rc && cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = DBP_ERR_CUDA;
     if (!rc) {
-        int crc = cudaEventRecord(B->fork, B->cap) == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
-        for (size_t gi = 0; gi < B->groups.size() && !crc; ++gi) {
-            BatchGroupHost &g = B->groups[gi];
-            if (cudaStreamWaitEvent(g.stream, B->fork, 0) != cudaSuccess) crc = DBP_ERR_CUDA;
-            if (!crc) crc = launch_group(g, B->d_counters + gi, B->d_error, B->max_spins, g.stream);
-            if (!crc && cudaEventRecord(g.done, g.stream) != cudaSuccess) crc = DBP_ERR_CUDA;
-            if (!crc && cudaStreamWaitEvent(B->cap, g.done, 0) != cudaSuccess) crc = DBP_ERR_CUDA;
-        }
+        int crc = launch_batch_unified(B->d_groups, B->d_units, B->n_units, B->d_counter, B->d_error, B->max_spins,
+                                       B->grid, B->cap);
         cudaGraph_t graph = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(B->cap, &graph);
         if (!crc && ec != cudaSuccess) crc = DBP_ERR_CUDA;
@@ -213,7 +183,7 @@ extern "C" int dbp_batch_run(dbp_batch_t *batch, dbp_stream_t stream) {
     if (!batch || !batch->impl) return DBP_ERR_ARG;
     BatchImpl *B = batch->impl;
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemsetAsync(B->d_counters, 0, sizeof(unsigned long long) * B->groups.size(), st) != cudaSuccess ||
+    if (cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned long long), st) != cudaSuccess ||
         cudaMemsetAsync(B->d_error, 0, sizeof(int), st) != cudaSuccess)
         return DBP_ERR_CUDA;
     // publish flags (any non-zero value means published): all set now, or all cleared for
@@ -229,7 +199,7 @@ extern "C" int dbp_batch_publish(dbp_batch_t *batch, int job, dbp_stream_t strea
     BatchImpl *B = batch->impl;
     cudaStream_t st = (cudaStream_t)stream;
     // after the flags were cleared by dbp_batch_run; a copy (no kernel) so that it
-    // proceeds while the persistent kernels occupy the SMs
+    // proceeds while the persistent kernel occupies the SMs
     if (cudaStreamWaitEvent(st, B->reset_done, 0) != cudaSuccess ||
         cudaMemcpyAsync(B->d_ready + job, B->h_one, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return DBP_ERR_CUDA;

@@ -156,7 +156,10 @@ __device__ __forceinline__ float joint_intensity(float2 y0, float2 y1) {
     return fmaf(y0.x, y0.x, fmaf(y0.y, y0.y, fmaf(y1.x, y1.x, y1.y * y1.y)));
 }
 
-template <int N>
+// GRP: the block is handled by a sub-group of N / 16 threads of a larger CTA (several
+// blocks side by side, each with its own shared-memory slice), synchronised with the
+// named barrier bar_id; otherwise by the whole CTA with __syncthreads.
+template <int N, bool GRP = false>
 struct Blk {
     using G = Geo<N>;
     static constexpr int N0 = G::N0, N1 = G::N1, N2 = G::N2, T = G::T, S1 = G::S1;
@@ -172,6 +175,15 @@ struct Blk {
     float *sa;     // current step's taps gamma_eff c_i (shared, broadcast reads)
     int t;
     uint32_t twt = 0;   // TMEM address of this thread's pass-1 twiddles (twiddles_to_tmem)
+    int bar_id = 0;     // GRP: named barrier of the sub-group (1 .. 15)
+
+    // barrier over the threads that handle this block
+    __device__ __forceinline__ void sync() const {
+        if constexpr (GRP)
+            asm volatile("bar.sync %0, %1;\n" ::"r"(bar_id), "n"(G::T) : "memory");
+        else
+            __syncthreads();
+    }
 
     __device__ __forceinline__ Blk(unsigned char *smem, int tid)
         : xs(reinterpret_cast<float4 *>(smem)),
@@ -711,12 +723,12 @@ struct Blk {
                 if (j == N2 - 1 && (T < G::HALO || i == C1 - 1) && e >= N - G::HALO)
                     sP[pphys(e - N + G::HALO)] = pk;
             }
-        __syncthreads();
+        sync();
         if constexpr (N >= 8192)
             fir16h_pairs(sP, tharr(), a, n_tapblk);
         else
             fir16h(sP, tharr(), a, n_tapblk);
-        __syncthreads();
+        sync();
     }
 
     // The same with P in farr(0) (no halo, the wrapping fir16) and theta into farr(1): the
@@ -737,13 +749,13 @@ struct Blk {
                 }
                 sP[pphys(pos1(i, j))] = pk;
             }
-        __syncthreads();
+        sync();
 #ifdef DBP_FIR_TC
         fir_tc(sP, farr(1), a, n_tapblk);
 #else
         fir16(sP, farr(1), a, n_tapblk);
 #endif
-        __syncthreads();
+        sync();
     }
 };
 

@@ -166,16 +166,21 @@ int dev_alloc(void **p, size_t bytes);
 int build_h_tables(PlanImpl &P);
 void fill_fwd_params(const PlanImpl &P, FwdParams &p);
 
-int prepare_batch_512(long long n_items, int *grid);
-int launch_batch_512(const BatchJob *, int, long long, unsigned long long *, int *, int, int, cudaStream_t);
-int prepare_batch_1024(long long n_items, int *grid);
-int launch_batch_1024(const BatchJob *, int, long long, unsigned long long *, int *, int, int, cudaStream_t);
-int prepare_batch_2048(long long n_items, int *grid);
-int launch_batch_2048(const BatchJob *, int, long long, unsigned long long *, int *, int, int, cudaStream_t);
-int prepare_batch_4096(long long n_items, int *grid);
-int launch_batch_4096(const BatchJob *, int, long long, unsigned long long *, int *, int, int, cudaStream_t);
-int prepare_batch_8192(long long n_items, int *grid);
-int launch_batch_8192(const BatchJob *, int, long long, unsigned long long *, int *, int, int, cudaStream_t);
+// Uneven batches: one persistent kernel over work units of every block length (batch_kernel.cu).
+struct BatchGroupDev {
+    const BatchJob *jobs;   // the group's jobs, item0 ascending
+    int n_jobs;
+    int N;                  // block length of the group
+};
+struct BatchUnit {
+    long long item0;        // first item (job, waveform, block) of the unit within its group
+    int group;
+    int count;              // items in the unit: at most batch_unit_blocks(N)
+};
+int batch_unit_blocks(int N);
+int prepare_batch_unified(int *grid);
+int launch_batch_unified(const BatchGroupDev *groups, const BatchUnit *units, long long n_units,
+                         unsigned long long *counter, int *error, int max_spins, int grid, cudaStream_t st);
 
 // Kernel launchers (one translation unit per block length).
 int launch_fwd_512(const FwdParams &, int n_wave, bool essfm, cudaStream_t);

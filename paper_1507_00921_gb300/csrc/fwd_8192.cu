@@ -6,11 +6,3 @@ int launch_fwd_8192(const FwdParams &p, int n_wave, bool essfm, cudaStream_t st)
     return launch_fwd_n<8192>(p, n_wave, essfm, st);
 }
 }  // namespace dbp
-
-namespace dbp {
-int prepare_batch_8192(long long n_items, int *grid) { return prepare_batch_n<8192>(n_items, grid); }
-int launch_batch_8192(const BatchJob *jobs, int n_jobs, long long n_items, unsigned long long *counter, int *error,
-                  int max_spins, int grid, cudaStream_t st) {
-    return launch_batch_n<8192>(jobs, n_jobs, n_items, counter, error, max_spins, grid, st);
-}
-}  // namespace dbp

@@ -22,8 +22,8 @@ namespace dbp {
 // Input window of overlap-save block (waveform w, block b) into registers (global
 // loads only, no shared memory).  SINGLE: a one-polarization waveform [n]; the two
 // polarization lanes carry blocks b and b + 1.
-template <int N, bool SINGLE = false>
-__device__ __forceinline__ void load_block(const FwdParams &p, const Blk<N> &blk, int w, int b,
+template <int N, bool SINGLE = false, class BK = Blk<N>>
+__device__ __forceinline__ void load_block(const FwdParams &p, const BK &blk, int w, int b,
                                            typename Blk<N>::Regs &v) {
     const long long n = p.n;
     const float2 *__restrict__ in = p.in + (size_t)w * (SINGLE ? 1 : 2) * n;
@@ -35,8 +35,8 @@ __device__ __forceinline__ void load_block(const FwdParams &p, const Blk<N> &blk
 // the previous block's last shared-memory access (and, with bulk stores, since its
 // output copy finished reading the staging buffer).  SINGLE: each lane has its own
 // intensity P = |y|^2, filter and phase.
-template <int N, bool ESSFM, bool SINGLE = false, bool FAST = false, bool TM = false>
-__device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, int w, int b,
+template <int N, bool ESSFM, bool SINGLE = false, bool FAST = false, bool TM = false, class BK = Blk<N>>
+__device__ __forceinline__ void compute_block(const FwdParams &p, BK &blk, int w, int b,
                                               typename Blk<N>::Regs &v) {
     using B = Blk<N>;
     const long long n = p.n;
@@ -44,25 +44,25 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
 
     MidMulH<N> mid{blk.sH};
     for (int s = 0; s < p.n_steps; ++s) {
-        if (ESSFM && s > 0) __syncthreads();   // previous step's theta and tap reads are done
+        if (ESSFM && s > 0) blk.sync();   // previous step's theta and tap reads are done
         if (ESSFM) blk.stage_taps(p.taps + p.taps_stride * s, p.taps_stride);
         blk.template pass1_fwd<TM>(v);
-        __syncthreads();
+        blk.sync();
         blk.template pass2<false, TM && ESSFM>();
         cp_async_wait_all();
-        __syncthreads();   // pass-2 results and H_s visible
+        blk.sync();   // pass-2 results and H_s visible
         blk.pass3(mid);
-        __syncthreads();
+        blk.sync();
         if (p.h_stride != 0 && s + 1 < p.n_steps) blk.prefetch_h(p.H + p.h_stride * (s + 1));
         blk.template pass2<true, TM && ESSFM>();
-        __syncthreads();
+        blk.sync();
         blk.template pass1_inv<TM>(v);
         if (p.linear_only) continue;   // FFE: dispersion compensation only
 
         // ---- nonlinear sub-step
         const float *__restrict__ a = p.taps + p.taps_stride * s;
         if constexpr (ESSFM && !SINGLE) {
-            __syncthreads();   // block buffer free: P and theta reuse it
+            blk.sync();   // block buffer free: P and theta reuse it
             blk.essfm_theta_fwd(v, blk.sa, p.n_tapblk);
             const float *sT = blk.tharr();
 #pragma unroll
@@ -75,7 +75,7 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
                 }
         } else if constexpr (ESSFM) {
             const float *sT = blk.tharr();
-            __syncthreads();   // block buffer free
+            blk.sync();   // block buffer free
             blk.template essfm_theta_fwd<0>(v, blk.sa, p.n_tapblk);
 #pragma unroll
             for (int i = 0; i < B::C1; ++i)
@@ -121,7 +121,7 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
         // the block buffer, then one thread copies each half to its place in `out`
         const int V = p.valid;
         float2 *stage = reinterpret_cast<float2 *>(blk.xs);
-        __syncthreads();   // all reads of P / theta / the block buffer are done
+        blk.sync();   // all reads of P / theta / the block buffer are done
 #pragma unroll
         for (int i = 0; i < B::C1; ++i)
 #pragma unroll
@@ -132,8 +132,8 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
                 stage[V + e - h] = v[1][i][j];
             }
         fence_proxy_async_smem();
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        blk.sync();
+        if (blk.t == 0) {
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
                 const long long g0 = (long long)(b + (SINGLE ? l : 0)) * V;
@@ -163,15 +163,15 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, Blk<N> &blk, i
 }
 
 // One block from load to output (batched launches): load, then compute.
-template <int N, bool ESSFM, bool SINGLE = false>
-__device__ __forceinline__ void process_block(const FwdParams &p, Blk<N> &blk, int w, int b) {
+template <int N, bool ESSFM, bool SINGLE = false, class BK = Blk<N>>
+__device__ __forceinline__ void process_block(const FwdParams &p, BK &blk, int w, int b) {
     typename Blk<N>::Regs v;
     load_block<N, SINGLE>(p, blk, w, b, v);
     if (ESSFM && p.bulk_store) {   // the previous block's output copy must have read shared memory
-        if (threadIdx.x == 0) bulk_wait_read_all();
-        __syncthreads();
+        if (blk.t == 0) bulk_wait_read_all();
+        blk.sync();
     }
-    compute_block<N, ESSFM, SINGLE>(p, blk, w, b, v);
+    compute_block<N, ESSFM, SINGLE, false, false, BK>(p, blk, w, b, v);
 }
 
 // Persistent over blocks: CTA c processes blocks c, c + gridDim.x, ...  The twiddle
@@ -281,92 +281,4 @@ int launch_fwd_n(const FwdParams &p, int n_wave, bool essfm, cudaStream_t st) {
 
 }  // namespace dbp
 
-namespace dbp {
 
-// Persistent batched DBP over many jobs (plans) of block length N: each CTA pops
-// (job, waveform, block) items from a device counter until the size group is done.
-// Every job has a publish flag; a CTA waits for it with a bounded spin (nanosleep
-// between polls, at most max_spins polls) and, if it never appears, records
-// DBP_ERR_TIMEOUT in *error and skips the item.  Once an error is recorded, waiting
-// CTAs give up immediately.
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::T, Geo<N>::MINB)
-    dbp_batch_kernel(const BatchJob *__restrict__ jobs, int n_jobs, long long n_items,
-                     unsigned long long *counter, int *error, int max_spins) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ FwdParams sp;
-    __shared__ long long s_item;
-    __shared__ int s_job, s_ok, s_essfm, s_w, s_b;
-    Blk<N> blk(smem_raw, threadIdx.x);
-    const int t = threadIdx.x;
-    blk.load_tables(jobs[0].p.twA, jobs[0].p.twB, jobs[0].p.tw2);
-    for (;;) {
-        if (t == 0) s_item = (long long)atomicAdd(counter, 1ull);
-        __syncthreads();
-        const long long item = s_item;
-        if (item >= n_items) break;
-        if (t == 0) {
-            int lo = 0, hi = n_jobs - 1;                 // last job with item0 <= item
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (jobs[mid].item0 <= item) lo = mid; else hi = mid - 1;
-            }
-            const BatchJob &J = jobs[lo];
-            int ok = 1;
-            const volatile int *flag = J.ready;
-            for (int spins = 0; *flag == 0;) {
-                if (*(volatile int *)error != 0 || ++spins > max_spins) {
-                    atomicCAS(error, 0, DBP_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(1000);
-            }
-            __threadfence();
-            s_ok = ok;
-            s_job = lo;
-            s_essfm = J.essfm;
-            sp = J.p;
-            const long long local = item - J.item0;
-            s_w = (int)(local / J.p.n_blocks);
-            s_b = (int)(local - (long long)s_w * J.p.n_blocks);
-        }
-        __syncthreads();
-        if (s_ok) {
-            blk.prefetch_h(sp.H);
-            if (s_essfm)
-                process_block<N, true>(sp, blk, s_w, s_b);
-            else
-                process_block<N, false>(sp, blk, s_w, s_b);
-        }
-        __syncthreads();   // shared memory free for the next item
-    }
-}
-
-// Grid of the persistent batch kernel (one wave of resident CTAs, at most n_items);
-// also opts the kernel into its shared memory.  Call before any stream capture.
-template <int N>
-int prepare_batch_n(long long n_items, int *grid) {
-    using G = Geo<N>;
-    static unsigned long long done = 0;
-    if (!set_smem_once(dbp_batch_kernel<N>, G::SMEM, done)) return DBP_ERR_CUDA;
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dbp_batch_kernel<N>, G::T, G::SMEM) != cudaSuccess)
-        return DBP_ERR_CUDA;
-    long long g = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    if (g > n_items) g = n_items;
-    *grid = (int)(g < 1 ? 1 : g);
-    return DBP_OK;
-}
-
-template <int N>
-int launch_batch_n(const BatchJob *jobs, int n_jobs, long long n_items, unsigned long long *counter, int *error,
-                   int max_spins, int grid, cudaStream_t st) {
-    using G = Geo<N>;
-    dbp_batch_kernel<N><<<(unsigned)grid, G::T, G::SMEM, st>>>(jobs, n_jobs, n_items, counter, error, max_spins);
-    return cudaGetLastError() == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
-}
-
-}  // namespace dbp
