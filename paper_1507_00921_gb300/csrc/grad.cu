@@ -65,6 +65,40 @@ __global__ void gather_kernel(const float4 *__restrict__ gblk, float2 *__restric
     gp[n + j] = make_float2(sz, sw);
 }
 
+// gather_kernel for waveforms short enough for 32-bit positions (n + nb V + N < 2^30):
+// one waveform per grid row, one division per unwrapped position, the periodic copies
+// (the blocks at the waveform ends wrap around) only where they reach.  Sums the covering
+// blocks in increasing block order, as gather_kernel does.
+__global__ void gather32_kernel(const float4 *__restrict__ gblk, float2 *__restrict__ gin, int n, int nb, int V,
+                                int half, int N, int boundary) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int w = blockIdx.y;
+    const float4 *gw = gblk + (size_t)w * nb * N;
+    float sx = 0.f, sy = 0.f, sz = 0.f, sw = 0.f;
+    const int end = (nb - 1) * V - half + N;            // unwrapped end of the last window
+    const bool per = boundary == DBP_PERIODIC;
+    // m = +1, 0, -1 in order of increasing block index: jp = j - n (first blocks), j, j + n (last blocks)
+#pragma unroll
+    for (int m = -1; m <= 1; ++m) {
+        if (m != 0 && !per) continue;
+        const int jp = j + m * n;
+        if (jp < -half || jp >= end) continue;
+        int bhi = (jp + half) / V;                       // last block whose window starts at or before jp
+        if (bhi > nb - 1) bhi = nb - 1;
+        int blo = bhi;
+        while (blo > 0 && (blo - 1) * V - half + N > jp) --blo;
+        for (int b = blo; b <= bhi; ++b) {
+            const int e = jp - (b * V - half);
+            const float4 g = gw[(size_t)b * N + e];
+            sx += g.x; sy += g.y; sz += g.z; sw += g.w;
+        }
+    }
+    float2 *gp = gin + (size_t)w * 2 * n;
+    gp[j] = make_float2(sx, sy);
+    gp[n + j] = make_float2(sz, sw);
+}
+
 // out[q] = sum over blocks b (fixed order) of part[b * stride + q], in FP64.
 __global__ void reduce_kernel(const float *__restrict__ part, long long blocks, int stride, double *out) {
     __shared__ double sm[256];
@@ -168,10 +202,18 @@ extern "C" int dbp_grad(dbp_plan_t *plan, const void *in, const void *grad_out, 
     int rc = launch_adj(P, q, nw, st);
     if (rc) return rc;
     if (grad_in) {
-        const long long total_s = P.signal.n_samples * nw;
-        gather_kernel<<<(unsigned)((total_s + 255) / 256), 256, 0, st>>>(
-            q.gblk, (float2 *)grad_in, P.signal.n_samples, P.info.n_blocks, P.info.valid, P.info.overlap / 2, N,
-            P.signal.boundary, nw);
+        const long long n = P.signal.n_samples;
+        const long long span = n + (long long)P.info.n_blocks * P.info.valid + N;
+        if (n >= N && span < (1LL << 30) && nw <= 65535) {
+            gather32_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)nw), 256, 0, st>>>(
+                q.gblk, (float2 *)grad_in, (int)n, P.info.n_blocks, P.info.valid, P.info.overlap / 2, N,
+                P.signal.boundary);
+        } else {
+            const long long total_s = n * nw;
+            gather_kernel<<<(unsigned)((total_s + 255) / 256), 256, 0, st>>>(
+                q.gblk, (float2 *)grad_in, n, P.info.n_blocks, P.info.valid, P.info.overlap / 2, N,
+                P.signal.boundary, nw);
+        }
     }
     double *sums = (double *)(sc + o_s);
     reduce_kernel<<<stride, 256, 0, st>>>(q.part, blocks, stride, sums);

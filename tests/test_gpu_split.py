@@ -107,3 +107,33 @@ def test_tcgen05_and_mma_sync_paths_agree(torch_cuda, prec, monkeypatch):
             assert plan.status() == 0
     rel = np.linalg.norm(outs[0] - outs[1]) / np.linalg.norm(outs[1])
     assert rel <= TOL[prec], rel
+
+
+@pytest.mark.parametrize("prec", ["split_fp16", "split_bf16"])
+@pytest.mark.parametrize("kind", ["nonuniform_steps", "ffe", "ssfm_zero"])
+def test_tcgen05_path_step_tables_and_methods(torch_cuda, prec, kind):
+    """The tcgen05 kernel's per-step H tables (unequal step lengths), the linear-only
+    method (FFE) and the SSFM with zero boundary against the FP64 oracle."""
+    torch = torch_cuda
+    from paper_1507_00921_gb300 import Plan
+    link = synth.link(20)
+    n = 4 * 2048 + 301
+    x = synth.random_field(2, n, synth.dbm_to_w(2.0), seed=97).astype(np.complex64)
+    kw = {"nonuniform_steps": dict(method="essfm", n_steps=3, n_taps=8, coeffs=coeffs(8),
+                                   step_len_m=np.array([0.4e6, 0.7e6, 0.5e6])),
+          "ffe": dict(method="ffe", n_steps=1),
+          "ssfm_zero": dict(method="ssfm", n_steps=4, boundary="zero")}[kind]
+    with Plan(link, FS, n, n_waveforms=2, fft_size=2048, precision=prec, dft_block=64, **kw) as plan:
+        got = plan.run(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.complex128)
+        ov = plan.info.overlap
+        assert plan.status() == 0
+    c = kw.get("coeffs")
+    nc = kw.get("n_taps", 0)
+    cfg = fiber.make_config(link, FS, kw["n_steps"], nc, 2048, coeffs=None if c is None else c.astype(np.float64),
+                            overlap=ov, boundary=kw.get("boundary", "periodic"), essfm=kw["method"] == "essfm",
+                            step_len_m=kw.get("step_len_m"),
+                            gamma_eff=np.zeros(1) if kw["method"] == "ffe" else None)
+    ref = odbp.dbp(x.astype(np.complex128), cfg)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print(f"\ntcgen05 {prec} {kind}: relative RMS {rel:.3e}")
+    assert rel <= TOL[prec], rel
