@@ -188,3 +188,66 @@ def test_tensor_memory_twiddles_match_table_twiddles(torch_cuda):
         assert batch.status() == 0
         batch.close()
     assert torch.equal(y_run, y_batch)
+
+
+def test_batch_every_block_length_against_runs_and_oracle(torch_cuda):
+    """One batch with jobs at every block length (512 ... 8192), so that the persistent
+    kernel runs units of 14, 7, 4, 2 and 1 blocks side by side: SSFM jobs and ESSFM jobs of
+    three steps take exactly the arithmetic of their own dbp_run (bitwise equal), ESSFM
+    jobs of one or two steps (hardware exponential in dbp_run) agree to 1e-6, and sampled
+    blocks of every job match the FP64 oracle."""
+    torch = torch_cuda
+    from paper_1507_00921_gb300 import Batch, Plan
+    specs = [  # spans, n, n_waveforms, plan keyword arguments
+        (1, 3000, 2, dict(method="ssfm", n_steps=3, fft_size=512)),
+        (1, 2501, 1, dict(method="essfm", n_steps=1, n_taps=8, fft_size=512, boundary="zero")),
+        (4, 9000, 2, dict(method="ssfm", n_steps=5, fft_size=1024, boundary="zero")),
+        (4, 7777, 3, dict(method="essfm", n_steps=3, n_taps=4, fft_size=1024)),
+        (10, 20000, 1, dict(method="essfm", n_steps=2, n_taps=16, fft_size=2048)),
+        (10, 12345, 2, dict(method="ssfm", n_steps=7, fft_size=2048)),
+        (20, 30000, 1, dict(method="essfm", n_steps=3, n_taps=8, fft_size=4096, boundary="zero")),
+        (40, 40000, 2, dict(method="ssfm", n_steps=4, fft_size=8192)),
+        (40, 33333, 1, dict(method="essfm", n_steps=1, n_taps=32, fft_size=8192)),
+    ]
+    plans, ins, outs, refs, kws = [], [], [], [], []
+    for k, (spans, n, nw, kw) in enumerate(specs):
+        kw = dict(kw)
+        nc = kw.get("n_taps", 0)
+        if nc:
+            c = 0.6 * np.exp(-np.arange(nc + 1) / 5.0)
+            kw["coeffs"] = (c / (c[0] + 2 * c[1:].sum())).astype(np.float32)
+        p = Plan(synth.link(spans), FS, n, n_waveforms=nw, **kw)
+        x = torch.from_numpy(synth.random_field(nw, n, synth.dbm_to_w(2.0), seed=700 + k).astype(np.complex64)).cuda()
+        plans.append(p)
+        ins.append(x)
+        outs.append(torch.zeros_like(x))
+        refs.append(p.run(x))
+        kws.append((synth.link(spans), kw))
+    with Batch(plans, ins, outs) as batch:
+        batch.run()
+        assert batch.status() == 0
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    for p, x, y, r, (link, kw) in zip(plans, ins, outs, refs, kws):
+        if kw["method"] == "ssfm" or kw["n_steps"] >= 3:
+            assert torch.equal(y, r), kw
+        else:
+            assert (y - r).abs().max().item() <= 1e-6 * r.abs().max().item(), kw
+        info = p.info
+        c = kw.get("coeffs")
+        cfg = fiber.make_config(link, FS, kw["n_steps"], kw.get("n_taps", 0), kw["fft_size"],
+                                coeffs=None if c is None else c.astype(np.float64), overlap=info.overlap,
+                                boundary=kw.get("boundary", "periodic"), essfm=kw["method"] == "essfm")
+        xs, ys = x.cpu().numpy(), y.cpu().numpy()
+        n, v = xs.shape[-1], info.valid
+        ids = np.unique(np.concatenate([[0, info.n_blocks - 1], rng.integers(0, info.n_blocks, 2)]))
+        ref = odbp.dbp_blocks(xs[-1].astype(np.complex128), cfg, ids)
+        for j, b in enumerate(ids):
+            lo, hi = b * v, min((b + 1) * v, n)
+            got = ys[-1][:, lo:hi].astype(np.complex128)
+            want = ref[j][:, : hi - lo]
+            rms = np.sqrt(np.mean(np.abs(want) ** 2))
+            assert np.sqrt(np.mean(np.abs(got - want) ** 2)) / rms <= 1e-5, (kw, b)
+            assert np.max(np.abs(got - want)) / rms <= 1e-4, (kw, b)
+    for p in plans:
+        p.close()
