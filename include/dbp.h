@@ -101,7 +101,11 @@ typedef struct {
     const double *step_len_m;   /* host [n_steps] step lengths (sum should be the link
                                    length) or NULL for uniform L / N_s                   */
     const double *gamma_eff;    /* host [n_steps] gamma*manakov*dz_eff overrides or NULL  */
-    int32_t fft_size;           /* N in {512,1024,2048,4096,8192}                        */
+    int32_t fft_size;           /* N in {512,1024,2048,4096,8192}, or 0 (FP32 only): the
+                                   supported N minimising Section III's operation count
+                                   per output sample, N (8 log2 N + 21 + N_c) / (N - O)
+                                   (FFE: 8 log2 N + 8), among those above the overlap O;
+                                   dbp_plan_info.fft_size reports the choice            */
     int32_t overlap;            /* O: 0 = rule ceil(M) + 2 N_s N_c rounded up to a
                                    multiple of 8; else a multiple of 4 in [0, N)        */
     int32_t precision;          /* DBP_FP32, DBP_SPLIT_BF16 or DBP_SPLIT_FP16            */

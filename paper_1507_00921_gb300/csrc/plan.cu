@@ -137,7 +137,8 @@ static int validate(const dbp_link *link, const dbp_signal *sig, const dbp_steps
     if (st->coeffs_per_step != 0 && st->coeffs_per_step != 1) return DBP_ERR_ARG;
     if (st->precision != DBP_FP32 && st->precision != DBP_SPLIT_BF16 && st->precision != DBP_SPLIT_FP16)
         return DBP_ERR_ARG;
-    if (!supported_n(st->fft_size)) return DBP_ERR_INFEASIBLE;
+    if (st->fft_size != 0 && !supported_n(st->fft_size)) return DBP_ERR_INFEASIBLE;
+    if (st->fft_size == 0 && st->precision != DBP_FP32) return DBP_ERR_UNSUPPORTED;
     if (st->precision != DBP_FP32) {
         const int N = st->fft_size, NA = st->dft_block;
         if (N < 1024 || N > 4096 || (NA != 64 && NA != 128 && NA != 256) || N / NA < 4 || N / NA > 32)
@@ -193,12 +194,29 @@ int describe(const dbp_link *link, const dbp_signal *sig, const dbp_steps *st, d
         if (need > 0x3fffffff) return DBP_ERR_INFEASIBLE;
         o = (int)(((need + 7) / 8) * 8);
     }
-    if (o >= st->fft_size) return DBP_ERR_INFEASIBLE;
-    const int valid = st->fft_size - o;
+    int fft = st->fft_size;
+    if (fft == 0) {
+        // Section III: the block length minimising the operation count per output
+        // sample, N (8 log2 N + 21 + N_c) / (N - O) (FFE: 8 log2 N + 8), over the
+        // supported lengths that exceed the overlap
+        const double extra = st->method == DBP_FFE ? 8.0 : 21.0 + (st->method == DBP_ESSFM ? st->n_taps : 0);
+        double best = 0.0;
+        for (int cand = 512; cand <= 8192; cand *= 2) {
+            if (o >= cand) continue;
+            const double cost = cand * (8.0 * log2((double)cand) + extra) / (double)(cand - o);
+            if (fft == 0 || cost < best) {
+                fft = cand;
+                best = cost;
+            }
+        }
+        if (fft == 0) return DBP_ERR_INFEASIBLE;
+    }
+    if (o >= fft) return DBP_ERR_INFEASIBLE;
+    const int valid = fft - o;
     const long long nb = (sig->n_samples + valid - 1) / valid;
     if (nb * sig->n_waveforms > 0x7fffffffLL) return DBP_ERR_ARG;
     if (info) {
-        info->fft_size = st->fft_size;
+        info->fft_size = fft;
         info->overlap = o;
         info->valid = valid;
         info->n_blocks = (int32_t)nb;
@@ -333,7 +351,7 @@ static int make_plan(const dbp_link *link, const dbp_signal *sig, const dbp_step
     P.dft_block = st->precision == DBP_FP32 ? 0 : st->dft_block;
     P.n_tapblk = st->method == DBP_ESSFM ? tap_blocks(st->n_taps) : 0;
     P.taps_stride = 1 + 8 * P.n_tapblk;
-    const int ns = st->n_steps, N = st->fft_size;
+    const int ns = st->n_steps, N = info.fft_size;
     P.step_dz = (double *)malloc(sizeof(double) * ns);
     P.step_geff = (double *)malloc(sizeof(double) * ns);
     P.coeffs = (float *)malloc(sizeof(float) * (size_t)ns * (st->n_taps + 1));

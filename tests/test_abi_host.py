@@ -110,3 +110,22 @@ def test_null_arguments_and_strerror():
     assert lib.dbp_strerror(-99) == b"unknown error"
     info = _lib.dbp_plan_info()
     assert lib.dbp_plan_describe(None, None, None, C.byref(info), None, None) == _lib.DBP_ERR_ARG
+
+
+def test_block_length_zero_takes_the_section_iii_optimum():
+    """fft_size = 0: the planner picks the supported block length that minimises the
+    operation count per output sample of Section III, N (8 log2 N + 21 + N_c) / (N - O),
+    among those above the overlap (host only, no GPU)."""
+    import synth
+    from paper_1507_00921_gb300 import complexity, describe
+    fs = synth.SAMPLE_RATE
+    for spans, method, ns, nc in [(40, "essfm", 1, 32), (10, "essfm", 1, 8), (40, "ssfm", 20, 0), (2, "ssfm", 3, 0),
+                                  (20, "essfm", 2, 16), (40, "ffe", 1, 0)]:
+        info = describe(synth.link(spans), fs, 1 << 16, method=method, n_steps=ns, n_taps=nc, fft_size=0)
+        o = info.overlap
+        cands = [n for n in (512, 1024, 2048, 4096, 8192) if n > o]
+        cost = {n: complexity.mults_per_sample(n, o, nc, ffe=method == "ffe") for n in cands}
+        assert info.fft_size == min(cost, key=cost.get), (spans, method, info.fft_size, cost)
+        assert info.valid == info.fft_size - o
+    # N = 8M is near-optimal in Section III; at 3200 km (M ~ 1368) that is the largest length
+    assert describe(synth.link(40), fs, 1 << 16, method="essfm", n_taps=32, fft_size=0).fft_size == 8192

@@ -266,3 +266,22 @@ def test_unaligned_buffers_match_aligned(torch_cuda, n_pols):
         torch.cuda.synchronize()
     assert torch.equal(ya, yu)
     assert ybuf[0].item() == 0
+
+
+def test_block_length_chosen_by_the_planner(torch_cuda):
+    """fft_size = 0 (the Section III operation-count optimum chosen by the planner) runs the
+    chosen block length and matches the oracle at that geometry."""
+    from paper_1507_00921_gb300 import Plan
+    torch = torch_cuda
+    link = synth.link(20)
+    n = 30000
+    c = 0.6 * np.exp(-np.arange(17) / 5.0)
+    kw = dict(method="essfm", n_steps=2, n_taps=16, coeffs=(c / (c[0] + 2 * c[1:].sum())).astype(np.float32))
+    x = synth.random_field(2, n, synth.dbm_to_w(2.0), seed=321)
+    with Plan(link, FS, n, n_waveforms=2, fft_size=0, **kw) as plan:
+        got = plan.run(torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy().astype(np.complex128)
+        info = plan.info
+    assert info.fft_size in (2048, 4096, 8192) and info.overlap < info.fft_size
+    cfg = oracle_cfg(link, dict(kw, fft_size=info.fft_size), info)
+    rel_rms, max_rel = compare(got, odbp.dbp(x, cfg))
+    assert rel_rms <= TOL_RMS and max_rel <= TOL_MAX, (rel_rms, max_rel)
