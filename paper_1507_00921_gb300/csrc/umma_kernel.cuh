@@ -17,10 +17,10 @@
 // parts of the 16-bit type, x = hi + lo (hi the rounding of x, lo that of the
 // remainder), and three products are accumulated in FP32 in two TMEM accumulators,
 // D_hh = A_hi B_hi and D_x = A_hi B_lo + A_lo B_hi (so that the small cross terms round
-// at their own magnitude), added once on readback.  Before each GEMM the tile is scaled by a power
-// of two (exact) so that its largest possible value is about 2^12: no value can
-// overflow FP16, the remainders of all but negligibly small values stay normal, and a
-// hi + lo pair keeps ~22 significant bits (BF16: ~16).
+// at their own magnitude), added once on readback.  Before each GEMM the tile is scaled
+// by a power of two (exact) so that its largest possible value is about 2^12: no value
+// can overflow FP16, the remainders of all but negligibly small values stay normal, and
+// a hi + lo pair keeps ~22 significant bits (BF16: ~16).
 //
 // One CTA (256 threads) owns one 128-row tile at a time: G = 64 / NB overlap-save
 // blocks, both polarizations.  Shared memory: the time-domain tile (float2
