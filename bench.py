@@ -781,12 +781,41 @@ def run_case(name: str):
     (not a benchmark): ``split`` the tcgen05 split-FP16 DFT-GEMM kernel (800 km ESSFM N_s=1
     N_c=16, N=1024, N_a=64, 64 x 2^15 samples), ``adjoint`` the reverse-mode kernel (3200 km
     ESSFM N_s=1 N_c=16, N=4096, 64 x 2^17 samples), ``forward`` the headline kernel (3200 km
-    ESSFM N_s=1 N_c=32, N=8192, 16 x 2^19 samples)."""
+    ESSFM N_s=1 N_c=32, N=8192, 16 x 2^19 samples), ``batch`` the uneven-batch kernel (64
+    jobs of the uneven workload, each at the shortest block length of at least twice its
+    overlap)."""
     import torch
-    from paper_1507_00921_gb300 import Plan
+    from paper_1507_00921_gb300 import Batch, Plan, describe
     gen = torch.Generator(device="cuda")
     gen.manual_seed(synth.BASE_SEED + 9)
     amp = math.sqrt(synth.dbm_to_w(LAUNCH_DBM))
+    if name == "batch":
+        def shortest(link, n, kw):
+            for f in (1024, 2048, 4096):
+                try:
+                    if 2 * describe(link, synth.SAMPLE_RATE, n, fft_size=f, **kw).overlap <= f:
+                        return f
+                except Exception:
+                    continue
+            return 8192
+        plans, ins, outs = [], [], []
+        for jb in synth.batch_jobs(64, synth.BASE_SEED + 5):
+            link = synth.link(jb["n_spans"])
+            n = jb["n_symbols"] * synth.SPS
+            kw = dict(method=jb["method"], n_steps=jb["n_steps"], n_taps=jb["n_taps"],
+                      coeffs=essfm_coeffs(jb["n_taps"]) if jb["n_taps"] else None)
+            plans.append(Plan(link, synth.SAMPLE_RATE, n, fft_size=shortest(link, n, kw), **kw))
+            ins.append(torch.randn((1, 2, n), dtype=torch.complex64, device="cuda", generator=gen) * amp)
+            outs.append(torch.empty_like(ins[-1]))
+        with Batch(plans, ins, outs) as batch:
+            for _ in range(3):
+                batch.run()
+            status = batch.status()
+        for pl in plans:
+            pl.close()
+        assert status == 0, status
+        print(json.dumps({"case": name, "jobs": len(plans), "status": status}))
+        return
     if name == "split":
         n, nw, kw, spans = 2 ** 15, 64, dict(method="essfm", n_steps=1, n_taps=16, coeffs=essfm_coeffs(16),
                                              fft_size=1024, precision="split_fp16", dft_block=64), 10
@@ -822,7 +851,7 @@ def main():
     ap.add_argument("--batch-jobs", type=int, default=256, help="uneven batched workload size (0: skip)")
     ap.add_argument("--no-extras", action="store_true", help="skip the precision-variant and adjoint lines")
     ap.add_argument("--sweep", action="store_true", help="3200 km method / steps / taps / block-length sweep")
-    ap.add_argument("--case", choices=["split", "adjoint", "forward"],
+    ap.add_argument("--case", choices=["split", "adjoint", "forward", "batch"],
                     help="run one small fixed workload of that kernel (for profiling) and exit")
     args = ap.parse_args()
     if args.case:
