@@ -13,9 +13,10 @@
 //     phi'_k = 2 pi^2 beta2 f_k^2
 //   overlap-and-save transposes to overlap-add of the block input gradients.
 // One CTA per block: a forward sweep stores each step's input (checkpoints); the reverse
-// sweep recomputes each step's linear sub-step from its checkpoint.  Per-block partial
-// sums of R_i and dL/ddz go to scratch and are reduced in a fixed order, so the result
-// is bitwise reproducible.  At N = 4096 the kernel runs two CTAs per SM (128 registers a
+// sweep recomputes each step's linear sub-step from its checkpoint.  Per-warp partial
+// sums of R_i and dL/ddz go to scratch (no CTA barrier) and are reduced in a fixed
+// order, so the result is bitwise reproducible.  ESSFM plans of at most two steps use the
+// forward kernel's hardware exponential, so the gradient is that of what dbp_run computes.  At N = 4096 the kernel runs two CTAs per SM (128 registers a
 // thread) and keeps each thread's spectrum U and gradient g in tensor memory (tcgen05.st
 // / tcgen05.ld of its own TMEM lane, 256 columns per CTA) instead of global scratch;
 // y stays in global scratch.
@@ -37,9 +38,10 @@ struct AdjParams {
     float cphi;              // 2 pi^2 beta2 (f_s / N)^2
 };
 
-template <int N, int K>
-__device__ __forceinline__ void block_sum(float (&val)[K], float *red, float *dst, int t) {
-    constexpr int W = Geo<N>::T / 32;
+// Sum of val[k] over the warp; lane 0 writes the K sums to dst (the warp's own row of
+// partial sums: no barrier, the fixed-order FP64 reduction over all rows follows later).
+template <int K>
+__device__ __forceinline__ void warp_sum(float (&val)[K], float *dst) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         float x = val[k];
@@ -47,17 +49,10 @@ __device__ __forceinline__ void block_sum(float (&val)[K], float *red, float *ds
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         val[k] = x;
     }
-    if ((t & 31) == 0) {
+    if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) red[(t >> 5) * K + k] = val[k];
+        for (int k = 0; k < K; ++k) dst[k] = val[k];
     }
-    __syncthreads();
-    if (t < K) {
-        float s = 0.f;
-        for (int w = 0; w < W; ++w) s += red[w * K + t];
-        dst[t] = s;
-    }
-    __syncthreads();
 }
 
 // pass-3 operation of the recomputed linear sub-step: x H_s, and keep U = H' X
@@ -220,14 +215,13 @@ struct MidAdjointTM {
     }
 };
 
-template <int N, bool ESSFM>
+template <int N, bool ESSFM, bool FAST = false>
 __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel(const AdjParams q) {
     using B = Blk<N>;
     using G = Geo<N>;
     const FwdParams &p = q.f;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     B blk(smem_raw, threadIdx.x);
-    float *red = reinterpret_cast<float *>(smem_raw + G::SMEM);
     const int t = threadIdx.x;
     // N = 4096 (two CTAs per SM): U and g in tensor memory (256 columns per CTA: 128 per
     // thread, two threads a lane), y in global scratch
@@ -258,7 +252,8 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
     float4 *__restrict__ gb = q.gblk + (size_t)blkid * N;
     float4 *__restrict__ ub = q.uscr + (size_t)blkid * N;
     float4 *__restrict__ yb = q.yscr + (size_t)blkid * N;
-    float *__restrict__ part = q.part + (size_t)blkid * (ns * q.nr + ns);
+    // this warp's row of partial sums: R_{s,i} then dL/ddz_s
+    float *__restrict__ part = q.part + ((size_t)blkid * (G::T / 32) + (threadIdx.x >> 5)) * (ns * q.nr + ns);
 
     blk.prefetch_h(p.H);
     blk.load_tables(p.twA, p.twB, p.tw2);
@@ -324,7 +319,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
             for (int j = 0; j < B::N2; ++j) {
                 const int e = blk.pos1(i, j);
                 const float th = ESSFM ? blk.farr(1)[pphys(e)] : a0 * joint_intensity(v[0][i][j], v[1][i][j]);
-                const float2 ex = expj(th);
+                const float2 ex = expj<FAST>(th);
                 v[0][i][j] = cmul(v[0][i][j], ex);
                 v[1][i][j] = cmul(v[1][i][j], ex);
                 ck[e] = make_float4(v[0][i][j].x, v[0][i][j].y, v[1][i][j].x, v[1][i][j].y);
@@ -387,7 +382,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
                     for (int jj = 0; jj < 4; ++jj) {
                         const int j = 4 * q + jj;
                         const int e = blk.pos1(i, j);
-                        const float2 ex = expj(sT[pphys(e)]);
+                        const float2 ex = expj<FAST>(sT[pphys(e)]);
                         const float2 y0 = v[0][i][j], y1 = v[1][i][j];
                         const float2 z0 = cmul(y0, ex), z1 = cmul(y1, ex);
                         const float4 g = TM ? gq[jj] : gb[e];
@@ -417,7 +412,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
                         sk[4 * qd + 0] = fs.x; sk[4 * qd + 1] = fs.y; sk[4 * qd + 2] = fs.z; sk[4 * qd + 3] = fs.w;
                         r0[0] = fmaf(fs.x, fp.x, fmaf(fs.y, fp.y, fmaf(fs.z, fp.z, fmaf(fs.w, fp.w, r0[0]))));
                     }
-                    block_sum<N, 1>(r0, red, rp, t);
+                    warp_sum<1>(r0, rp);
                 }
                 for (int tb = 0; tb < p.n_tapblk; ++tb) {
                     const int i0 = 8 * tb;
@@ -439,7 +434,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
                         for (int r = 0; r < 16; ++r) x = fmaf(sk[r], lw[r - ii + 8] + rw[r + ii], x);
                         acc[ii - 1] = x;
                     }
-                    block_sum<N, 8>(acc, red, rp + 1 + i0, t);
+                    warp_sum<8>(acc, rp + 1 + i0);
                 }
                 blk.fir16(sS, blk.farr(1), blk.sa, p.n_tapblk);
             }
@@ -484,7 +479,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
                     if (TM && (j & 3) == 0) tm_load4(tm_g + 4 * j, gq);
                     const float2 y0 = v[0][i][j], y1 = v[1][i][j];
                     const float pk = joint_intensity(y0, y1);
-                    const float2 ex = expj(a0 * pk);
+                    const float2 ex = expj<FAST>(a0 * pk);
                     const float2 z0 = cmul(y0, ex), z1 = cmul(y1, ex);
                     const float4 g = TM ? gq[j & 3] : gb[e];
                     const float2 g0 = make_float2(g.x, g.y), g1 = make_float2(g.z, g.w);
@@ -495,7 +490,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
                     v[0][i][j] = make_float2(fmaf(dp2, y0.x, d0.x), fmaf(dp2, y0.y, d0.y));
                     v[1][i][j] = make_float2(fmaf(dp2, y1.x, d1.x), fmaf(dp2, y1.y, d1.y));
                 }
-            block_sum<N, 1>(r0, red, rp, t);
+            warp_sum<1>(r0, rp);
         }
         // linear adjoint: x conj(H'), with the step-length gradient
         __syncthreads();
@@ -519,7 +514,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         blk.pass1_inv(v);   // v = g_x
         {
             float dz[1] = {dzacc};
-            block_sum<N, 1>(dz, red, part + ns * q.nr + s, t);
+            warp_sum<1>(dz, part + ns * q.nr + s);
         }
         if (TM && s > 0) {   // the next (earlier) step's output gradient stays in TMEM
             auto gx = [&](int j) { return make_float4(v[0][0][j].x, v[0][0][j].y, v[1][0][j].x, v[1][0][j].y); };
@@ -545,11 +540,14 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
 template <int N>
 int launch_adj_n(const AdjParams &q, int n_wave, bool essfm, cudaStream_t st) {
     using G = Geo<N>;
-    static unsigned long long done_e = 0, done_s = 0;
-    const size_t smem = G::SMEM + (size_t)(G::T / 32) * 8 * sizeof(float);
+    static unsigned long long done_e = 0, done_s = 0, done_f = 0;
+    const size_t smem = G::SMEM;
     const long long grid = (long long)q.f.n_blocks * n_wave;
     if (grid <= 0 || grid > 0x7fffffffLL) return DBP_ERR_ARG;
-    if (essfm) {
+    if (essfm && q.f.fast_exp) {   // the forward kernel's exponential for plans of at most two steps
+        if (!set_smem_once(dbp_adj_kernel<N, true, true>, smem, done_f)) return DBP_ERR_CUDA;
+        dbp_adj_kernel<N, true, true><<<(unsigned)grid, G::T, smem, st>>>(q);
+    } else if (essfm) {
         if (!set_smem_once(dbp_adj_kernel<N, true>, smem, done_e)) return DBP_ERR_CUDA;
         dbp_adj_kernel<N, true><<<(unsigned)grid, G::T, smem, st>>>(q);
     } else {

@@ -4,11 +4,11 @@
 //
 // dbp_grad launches, on the caller's stream:
 //   1. dbp_adj_kernel: one CTA per overlap-save block; block input gradients and
-//      per-block partial sums of R_{s,i} = sum_k s_k S_{k,i} and dL/ddz_s to scratch;
+//      per-warp partial sums of R_{s,i} = sum_k s_k S_{k,i} and dL/ddz_s to scratch;
 //   2. gather_kernel: overlap-add of the block input gradients (Section III's
 //      overlap-and-save transposed), each input sample summing its covering blocks in
 //      block order;
-//   3. reduce_kernel: FP64 sums of the partials over blocks in a fixed order;
+//   3. reduce_kernel: FP64 sums of the partials over all warp rows in a fixed order;
 //   4. finalize_kernel: dL/dc_{s,i} = gamma_eff_s R_{s,i} (summed over steps when the
 //      coefficients are shared), dL/dgamma_eff_s = sum_i c_{s,i} R_{s,i}, dL/ddz_s.
 // No floating-point atomics: results are bitwise reproducible.
@@ -99,7 +99,8 @@ __global__ void gather32_kernel(const float4 *__restrict__ gblk, float2 *__restr
     gp[n + j] = make_float2(sz, sw);
 }
 
-// out[q] = sum over blocks b (fixed order) of part[b * stride + q], in FP64.
+// out[q] = sum over rows b (fixed order) of part[b * stride + q], in FP64 (one row of
+// partial sums per warp of each block).
 __global__ void reduce_kernel(const float *__restrict__ part, long long blocks, int stride, double *out) {
     __shared__ double sm[256];
     const int q = blockIdx.x;
@@ -176,7 +177,8 @@ extern "C" int dbp_grad(dbp_plan_t *plan, const void *in, const void *grad_out, 
     const size_t o_g = 0, o_u = al256(fld), o_y = o_u + al256(fld);
     const size_t o_c = o_y + al256(fld);
     const size_t o_p = o_c + al256(fld * (ns > 1 ? ns - 1 : 1));
-    const size_t o_s = o_p + al256(sizeof(float) * (size_t)blocks * stride);
+    const long long rows = blocks * (N / 512);   // one row of partial sums per warp of each block
+    const size_t o_s = o_p + al256(sizeof(float) * (size_t)rows * stride);
     const size_t total = o_s + al256(sizeof(double) * stride);
     if (P.adj_bytes < total) {
         if (P.d_adj) cudaFree(P.d_adj);
@@ -216,7 +218,7 @@ extern "C" int dbp_grad(dbp_plan_t *plan, const void *in, const void *grad_out, 
         }
     }
     double *sums = (double *)(sc + o_s);
-    reduce_kernel<<<stride, 256, 0, st>>>(q.part, blocks, stride, sums);
+    reduce_kernel<<<stride, 256, 0, st>>>(q.part, rows, stride, sums);
     finalize_kernel<<<1, 256, 0, st>>>(sums, P.d_craw, P.d_geff, ns, nt, nr, P.coeffs_per_step, d_coeffs, d_gamma_eff,
                                        d_step_len);
     return cudaGetLastError() == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
