@@ -8,7 +8,8 @@
 //   2. gather_kernel: overlap-add of the block input gradients (Section III's
 //      overlap-and-save transposed), each input sample summing its covering blocks in
 //      block order;
-//   3. reduce_kernel: FP64 sums of the partials over all warp rows in a fixed order;
+//   3. reduce_kernel, reduce_segments_kernel: FP64 sums of the partials over all warp
+//      rows (segment sums, then the sum of the segments), in a fixed order;
 //   4. finalize_kernel: dL/dc_{s,i} = gamma_eff_s R_{s,i} (summed over steps when the
 //      coefficients are shared), dL/dgamma_eff_s = sum_i c_{s,i} R_{s,i}, dL/ddz_s.
 // No floating-point atomics: results are bitwise reproducible.
@@ -99,20 +100,35 @@ __global__ void gather32_kernel(const float4 *__restrict__ gblk, float2 *__restr
     gp[n + j] = make_float2(sz, sw);
 }
 
-// out[q] = sum over rows b (fixed order) of part[b * stride + q], in FP64 (one row of
-// partial sums per warp of each block).
-__global__ void reduce_kernel(const float *__restrict__ part, long long blocks, int stride, double *out) {
+// Two-stage FP64 sum over the rows of partial sums (one row per warp of each block):
+// seg_sum[q * segs + g] = sum of part[b * stride + q] over the rows b of contiguous
+// segment g, then out[q] = sum of the segment sums in segment order.  The grid and the
+// order of every addition depend only on (rows, stride, segs), so the result is bitwise
+// reproducible.
+__global__ void reduce_kernel(const float *__restrict__ part, long long rows, int stride, int segs,
+                              double *__restrict__ seg_sum) {
     __shared__ double sm[256];
-    const int q = blockIdx.x;
+    const int q = blockIdx.x, g = blockIdx.y;
+    const long long per = (rows + segs - 1) / segs;
+    const long long b0 = (long long)g * per;
+    const long long b1 = b0 + per < rows ? b0 + per : rows;
     double acc = 0.0;
-    for (long long b = threadIdx.x; b < blocks; b += blockDim.x) acc += (double)part[(size_t)b * stride + q];
+    for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) acc += (double)part[(size_t)b * stride + q];
     sm[threadIdx.x] = acc;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[q] = sm[0];
+    if (threadIdx.x == 0) seg_sum[(size_t)q * segs + g] = sm[0];
+}
+
+__global__ void reduce_segments_kernel(const double *__restrict__ seg_sum, int stride, int segs, double *out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= stride) return;
+    double acc = 0.0;
+    for (int g = 0; g < segs; ++g) acc += seg_sum[(size_t)q * segs + g];
+    out[q] = acc;
 }
 
 __global__ void finalize_kernel(const double *sums, const float *craw, const double *geff, int ns, int nt, int nr,
@@ -179,7 +195,10 @@ extern "C" int dbp_grad(dbp_plan_t *plan, const void *in, const void *grad_out, 
     const size_t o_p = o_c + al256(fld * (ns > 1 ? ns - 1 : 1));
     const long long rows = blocks * (N / 512);   // one row of partial sums per warp of each block
     const size_t o_s = o_p + al256(sizeof(float) * (size_t)rows * stride);
-    const size_t total = o_s + al256(sizeof(double) * stride);
+    // segments of the first reduction stage: about 1024 rows each, at most 64
+    const int segs = (int)(rows / 1024 + 1 < 64 ? rows / 1024 + 1 : 64);
+    const size_t o_seg = o_s + al256(sizeof(double) * stride);
+    const size_t total = o_seg + al256(sizeof(double) * (size_t)stride * segs);
     if (P.adj_bytes < total) {
         if (P.d_adj) cudaFree(P.d_adj);
         P.d_adj = nullptr;
@@ -218,7 +237,9 @@ extern "C" int dbp_grad(dbp_plan_t *plan, const void *in, const void *grad_out, 
         }
     }
     double *sums = (double *)(sc + o_s);
-    reduce_kernel<<<stride, 256, 0, st>>>(q.part, rows, stride, sums);
+    double *seg_sum = (double *)(sc + o_seg);
+    reduce_kernel<<<dim3((unsigned)stride, (unsigned)segs), 256, 0, st>>>(q.part, rows, stride, segs, seg_sum);
+    reduce_segments_kernel<<<(stride + 127) / 128, 128, 0, st>>>(seg_sum, stride, segs, sums);
     finalize_kernel<<<1, 256, 0, st>>>(sums, P.d_craw, P.d_geff, ns, nt, nr, P.coeffs_per_step, d_coeffs, d_gamma_eff,
                                        d_step_len);
     return cudaGetLastError() == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
