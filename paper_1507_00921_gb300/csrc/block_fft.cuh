@@ -217,10 +217,15 @@ struct Blk {
     }
 
     // Copies one step's H table (N float2, 16-byte chunks) into padded shared memory.
+    // Warp w copies positions [512 w, 512 w + 512): exactly the ones its own threads read
+    // in pass 3 (16 positions a thread at N0 = 16; one polarization of 32 at N0 = 32), so
+    // a warp's own copies and a __syncwarp make them visible where pass 3 needs them.
     __device__ __forceinline__ void prefetch_h(const float2 *__restrict__ H) {
+        static_assert(T % 32 == 0 && N == 512 * (T / 32), "512 positions per warp");
+        const int e0 = 512 * (t >> 5) + 2 * (t & 31);
 #pragma unroll
-        for (int q = 0; q < (N / 2) / T; ++q) {
-            const int e = 2 * (t + T * q);
+        for (int q = 0; q < 8; ++q) {
+            const int e = e0 + 64 * q;
             cp_async16(sH + hphys<N0>(e), H + e);
         }
         cp_async_commit();

@@ -50,9 +50,12 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, BK &blk, int w
         blk.sync();
         blk.template pass2<false, TM && ESSFM>();
         cp_async_wait_all();
-        blk.sync();   // pass-2 results and H_s visible
+        // Passes 2 -> 3 -> 2' stay inside a warp: warp w's pass-2 columns write, and its
+        // pass-3 threads read, positions [512 w, 512 w + 512), and warp w copied the H_s
+        // entries of those positions itself.  A warp barrier orders them.
+        __syncwarp();
         blk.pass3(mid);
-        blk.sync();
+        __syncwarp();
         if (p.h_stride != 0 && s + 1 < p.n_steps) blk.prefetch_h(p.H + p.h_stride * (s + 1));
         blk.template pass2<true, TM && ESSFM>();
         blk.sync();
