@@ -299,9 +299,9 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         __syncthreads();
         blk.template pass2<false>();
         cp_async_wait_all();
-        __syncthreads();
+        __syncwarp();   // passes 2 -> 3 -> 2' stay inside a warp (as in the forward kernel)
         blk.pass3(mulh);
-        __syncthreads();
+        __syncwarp();
         blk.template pass2<true>();
         __syncthreads();
         blk.pass1_inv(v);
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         __syncthreads();
         blk.template pass2<false>();
         cp_async_wait_all();
-        __syncthreads();
+        __syncwarp();
         if constexpr (TM) {
             MidRecomputeTM<N> rec{blk.sH, tm_u};
             blk.pass3(rec);
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
             MidRecompute<N> rec{blk.sH, ub};
             blk.pass3(rec);
         }
-        __syncthreads();
+        __syncwarp();
         blk.template pass2<true>();
         __syncthreads();
         blk.pass1_inv(v);   // v = y
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         blk.pass1_fwd(v);
         __syncthreads();
         blk.template pass2<false>();
-        __syncthreads();
+        __syncwarp();
         float dzacc;
         if constexpr (TM) {
             MidAdjointTM<N> adj{blk.sH, tm_u, q.cphi, 0.f};
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
             blk.pass3(adj);
             dzacc = adj.acc;
         }
-        __syncthreads();
+        __syncwarp();
         blk.template pass2<true>();
         __syncthreads();
         blk.pass1_inv(v);   // v = g_x

@@ -211,3 +211,28 @@ def test_autograd_over_coeffs_gamma_and_step_lengths(torch_cuda):
             getattr(b, attr)[s] -= h
             fd = (loss_of(a) - loss_of(b)) / (2 * h)
             assert abs(got - fd) <= TOL * max(abs(fd), 1e-6), (attr, s, got, fd)
+
+
+def test_gradient_is_bitwise_reproducible(torch_cuda):
+    """Every partial sum is reduced in an order fixed by the problem's shape (per-warp rows,
+    segments of rows, then the segments in order) and the input gradient sums its covering
+    blocks in block order, so two calls, on two streams, give the same bits.  The size
+    (16 waveforms, N = 4096, eight warp rows per block) spans several reduction segments."""
+    torch = torch_cuda
+    from paper_1507_00921_gb300 import Plan
+    n, nw = 1 << 17, 16
+    x = torch.from_numpy(synth.random_field(nw, n, synth.dbm_to_w(2.0), seed=21).astype(np.complex64)).cuda()
+    v = torch.from_numpy(synth.random_field(nw, n, 1.0, seed=22).astype(np.complex64)).cuda()
+    with Plan(synth.link(40), FS, n, n_waveforms=nw, method="essfm", n_steps=2, n_taps=16, fft_size=4096,
+              coeffs=coeffs_for(16, 2, True).ravel(), coeffs_per_step=True) as plan:
+        assert plan.info.n_blocks * nw * 8 > 4 * 1024      # more than four reduction segments
+        first = plan.grad(x, v)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())          # the plan's scratch is shared by its calls
+        with torch.cuda.stream(s):
+            second = plan.grad(x, v, stream=s)
+        s.synchronize()
+        torch.cuda.synchronize()
+    for a, b in zip(first, second):
+        assert torch.equal(a, b)
+    assert all(torch.isfinite(torch.view_as_real(t) if t.is_complex() else t).all() for t in first)
