@@ -129,3 +129,13 @@ def test_block_length_zero_takes_the_section_iii_optimum():
         assert info.valid == info.fft_size - o
     # N = 8M is near-optimal in Section III; at 3200 km (M ~ 1368) that is the largest length
     assert describe(synth.link(40), fs, 1 << 16, method="essfm", n_taps=32, fft_size=0).fft_size == 8192
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU or oracle fallback: with the shared library absent (and no build allowed),
+    loading the binding raises instead of computing anything another way."""
+    from paper_1507_00921_gb300 import build as _build
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "missing" / "libdbp.so"))
+    with pytest.raises(RuntimeError, match="libdbp not built"):
+        _lib.load(build_if_needed=False)
