@@ -16,9 +16,10 @@
 // sweep recomputes each step's linear sub-step from its checkpoint.  Per-warp partial
 // sums of R_i and dL/ddz go to scratch (no CTA barrier) and are reduced in a fixed
 // order, so the result is bitwise reproducible.  ESSFM plans of at most two steps use the
-// forward kernel's hardware exponential, so the gradient is that of what dbp_run computes.  At N = 4096 the kernel runs two CTAs per SM (128 registers a
-// thread) and keeps each thread's spectrum U and gradient g in tensor memory (tcgen05.st
-// / tcgen05.ld of its own TMEM lane, 256 columns per CTA) instead of global scratch;
+// forward kernel's hardware exponential, so the gradient is that of what dbp_run
+// computes.  At N = 4096 (two CTAs per SM, 128 registers a thread) and N = 8192 (one)
+// each thread's spectrum U and gradient g live in tensor memory (tcgen05.st /
+// tcgen05.ld of its own TMEM lane, 128 columns a thread) instead of global scratch;
 // y stays in global scratch.
 #pragma once
 #include "block_fft.cuh"
@@ -123,10 +124,10 @@ struct MidAdjoint {
 };
 
 // Tensor memory as per-thread scratch of the reverse sweep (N = 4096: 256 threads, two
-// per TMEM lane, 192 columns each): the thread's U (its 16 pass-3 positions), y and the
-// gradient g (its 16 pass-1 positions), 64 32-bit columns each, one float4 (both
-// polarizations) per position.  Every access is to the thread's own positions, so TMEM
-// replaces the round trip through global memory.
+// per TMEM lane; N = 8192: 512 threads, four per lane; 128 columns a thread): the
+// thread's U (its pass-3 positions) and the gradient g (its 16 pass-1 positions, one
+// float4 of both polarizations per position), 64 32-bit columns each.  Every access is
+// to the thread's own positions, so TMEM replaces the round trip through global memory.
 __device__ __forceinline__ void tm_st16(uint32_t a, const uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -164,7 +165,9 @@ __device__ __forceinline__ void tm_load4(uint32_t a, float4 (&v)[4]) {
                            __uint_as_float(r[4 * j + 3]));
 }
 
-// MidRecompute with U kept in TMEM (pass 3 with N0 = 16: positions base .. base + 15)
+// MidRecompute with U kept in TMEM.  two: pass 3 with N0 = 16 (positions base .. base + 15,
+// both polarizations, one float4 per position); one: N0 = 32 (one polarization of
+// positions base .. base + 31, two complex values per float4).  64 columns either way.
 template <int N>
 struct MidRecomputeTM {
     const float2 *sH;
@@ -177,6 +180,18 @@ struct MidRecomputeTM {
                       make_float4(u0[4 * q + 1].x, u0[4 * q + 1].y, u1[4 * q + 1].x, u1[4 * q + 1].y),
                       make_float4(u0[4 * q + 2].x, u0[4 * q + 2].y, u1[4 * q + 2].x, u1[4 * q + 2].y),
                       make_float4(u0[4 * q + 3].x, u0[4 * q + 3].y, u1[4 * q + 3].x, u1[4 * q + 3].y));
+        tm_wait_st();
+    }
+    template <int R>
+    __device__ __forceinline__ void one(float2 (&u)[R], int pol, int base) {
+        static_assert(R == 32, "64 columns: 32 complex values of one polarization");
+        MidMulH<N>{sH}.one(u, pol, base);
+#pragma unroll
+        for (int q = 0; q < R / 8; ++q)
+            tm_store4(ucol + 16 * q, make_float4(u[8 * q].x, u[8 * q].y, u[8 * q + 1].x, u[8 * q + 1].y),
+                      make_float4(u[8 * q + 2].x, u[8 * q + 2].y, u[8 * q + 3].x, u[8 * q + 3].y),
+                      make_float4(u[8 * q + 4].x, u[8 * q + 4].y, u[8 * q + 5].x, u[8 * q + 5].y),
+                      make_float4(u[8 * q + 6].x, u[8 * q + 6].y, u[8 * q + 7].x, u[8 * q + 7].y));
         tm_wait_st();
     }
 };
@@ -213,6 +228,30 @@ struct MidAdjointTM {
             u1[2 * j + 1] = cmulc(u1[2 * j + 1], make_float2(h.z, h.w));
         }
     }
+    template <int R>
+    __device__ __forceinline__ void one(float2 (&u)[R], int pol, int base) {
+        static_assert(R == 32, "64 columns: 32 complex values of one polarization");
+        MidAdjoint<N> m{sH, nullptr, cphi, 0.f};
+#pragma unroll
+        for (int q = 0; q < R / 8; ++q) {
+            float4 uu[4];
+            tm_load4(ucol + 16 * q, uu);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int j = 8 * q + 2 * jj;
+                acc = fmaf(m.phi_prime(base + j), MidAdjoint<N>::mimag(u[j], make_float2(uu[jj].x, uu[jj].y)), acc);
+                acc = fmaf(m.phi_prime(base + j + 1), MidAdjoint<N>::mimag(u[j + 1], make_float2(uu[jj].z, uu[jj].w)),
+                           acc);
+            }
+        }
+        const float4 *hrow = reinterpret_cast<const float4 *>(sH + hphys<R>(base));
+#pragma unroll
+        for (int j = 0; j < R / 2; ++j) {
+            const float4 h = hrow[j];
+            u[2 * j] = cmulc(u[2 * j], make_float2(h.x, h.y));
+            u[2 * j + 1] = cmulc(u[2 * j + 1], make_float2(h.z, h.w));
+        }
+    }
 };
 
 template <int N, bool ESSFM, bool FAST = false>
@@ -223,15 +262,16 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
     extern __shared__ __align__(16) unsigned char smem_raw[];
     B blk(smem_raw, threadIdx.x);
     const int t = threadIdx.x;
-    // N = 4096 (two CTAs per SM): U and g in tensor memory (256 columns per CTA: 128 per
-    // thread, two threads a lane), y in global scratch
-    constexpr bool TM = (N == 4096);
+    // N = 4096 (two CTAs per SM) and N = 8192 (one): U and g in tensor memory (128 columns
+    // a thread: 256 columns per CTA at N = 4096, all 512 at N = 8192), y in global scratch
+    constexpr bool TM = (N == 4096 || N == 8192);
+    constexpr uint32_t TM_COLS = (uint32_t)G::T;   // 128 columns for each group of four warps
     __shared__ uint32_t s_tmem;
     uint32_t tcol = 0;
     if constexpr (TM) {
-        static_assert(Geo<N>::T == 256 && B::C1 == 1 && B::N2 == 16 && G::N0 == 16, "thread-own scratch layout");
+        static_assert((G::T == 256 || G::T == 512) && B::C1 == 1 && B::N2 == 16, "thread-own scratch layout");
         if (t < 32) {
-            tmem_alloc(&s_tmem, 256);
+            tmem_alloc(&s_tmem, TM_COLS);
             tmem_relinquish();
         }
         tmem_fence_before_sync();
@@ -533,7 +573,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         tmem_fence_before_sync();
         __syncthreads();
         tmem_fence_after_sync();
-        if (t < 32) tmem_dealloc(s_tmem, 256);
+        if (t < 32) tmem_dealloc(s_tmem, TM_COLS);
     }
 }
 

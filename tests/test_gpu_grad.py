@@ -52,6 +52,10 @@ CASES = [
     ("essfm3_nc8_N1024_nonuniform", 10, 4000, 1, dict(method="essfm", n_steps=3, n_taps=8, fft_size=1024,
                                                       step_len_m=np.array([2e5, 3.5e5, 2.5e5]))),
     ("essfm1_nc32_N8192", 40, 12000, 1, dict(method="essfm", n_steps=1, n_taps=32, fft_size=8192)),
+    # N = 8192 keeps U and g in tensor memory across the steps of the reverse sweep
+    ("essfm3_nc8_N8192_zero_perstep", 40, 17000, 1, dict(method="essfm", n_steps=3, n_taps=8, fft_size=8192,
+                                                         boundary="zero", coeffs_per_step=True)),
+    ("ssfm4_N8192", 40, 15000, 2, dict(method="ssfm", n_steps=4, fft_size=8192)),
     ("essfm2_nc4_N512_tiny_n", 2, 300, 1, dict(method="essfm", n_steps=2, n_taps=4, fft_size=512)),
 ]
 
