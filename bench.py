@@ -414,7 +414,8 @@ def precision_measure(torch, stream):
 
 def adjoint_measure(torch, stream):
     """Reverse mode (forward + adjoint kernels) over 3200 km: 64 waveforms of 2^16
-    symbols, ESSFM N_c = 16, N_s in {1, 2, 4}, N = 4096."""
+    symbols, ESSFM N_c = 16, N_s in {1, 2, 4}, N = 4096 (and the same at N = 8192 under
+    "n8192")."""
     from paper_1507_00921_gb300 import Plan
     n, nw = 2 ** 17, 64
     gen = torch.Generator(device="cuda")
@@ -423,11 +424,13 @@ def adjoint_measure(torch, stream):
         synth.dbm_to_w(2.0))
     g = torch.randn((nw, 2, n), dtype=torch.complex64, device="cuda", generator=gen)
     out = {}
-    for ns in (1, 2, 4):
-        with Plan(synth.link(N_SPANS), synth.SAMPLE_RATE, n, n_waveforms=nw, method="essfm", n_steps=ns,
-                  n_taps=16, coeffs=essfm_coeffs(16), fft_size=4096) as plan:
-            t = time_plan(torch, lambda: plan.grad(x, g, stream=stream), stream, reps=5)
-        out[f"n_steps_{ns}"] = round(nw * n / t / 1e6, 1)
+    for fft in (4096, 8192):
+        dst = out if fft == 4096 else out.setdefault("n8192", {})
+        for ns in (1, 2, 4):
+            with Plan(synth.link(N_SPANS), synth.SAMPLE_RATE, n, n_waveforms=nw, method="essfm", n_steps=ns,
+                      n_taps=16, coeffs=essfm_coeffs(16), fft_size=fft) as plan:
+                t = time_plan(torch, lambda: plan.grad(x, g, stream=stream), stream, reps=5)
+            dst[f"n_steps_{ns}"] = round(nw * n / t / 1e6, 1)
     out["workload"] = "3200 km ESSFM N_c=16, N=4096, 64 x 2^17 samples, input + coefficient + gamma + dz gradients"
     out["unit"] = UNIT
     return out
