@@ -273,6 +273,7 @@ int dbp_run_noalloc(const dbp_link *link, const dbp_signal *signal, const dbp_st
  * of all jobs are cut into work units (several blocks side by side for the shorter
  * block lengths), one persistent kernel pops the units of every block length from one
  * device counter, longest blocks first, and that kernel is captured in a CUDA graph.
+ * Every job's output is bitwise equal to what dbp_run of its plan writes.
  * Plans and buffers must stay alive and unchanged in place while the batch exists.
  * flags: 0, or DBP_BATCH_STREAMING: every job's input is read only after
  * dbp_batch_publish(job) (a producer may fill inputs while the batch runs).  A job that

@@ -91,7 +91,9 @@ __device__ __noinline__ void run_unit(unsigned char *smem, const BatchGroupDev &
     const int w = (int)(local / sp->n_blocks);
     const int b = (int)(local - (long long)w * sp->n_blocks);
     blk.prefetch_h(sp->H);
-    if (J.essfm)
+    if (J.essfm && sp->fast_exp)   // the same exponential as the job's own dbp_run
+        process_block<N, true, false, true>(*sp, blk, w, b);
+    else if (J.essfm)
         process_block<N, true, false>(*sp, blk, w, b);
     else
         process_block<N, false, false>(*sp, blk, w, b);

@@ -165,8 +165,9 @@ __device__ __forceinline__ void compute_block(const FwdParams &p, BK &blk, int w
         }
 }
 
-// One block from load to output (batched launches): load, then compute.
-template <int N, bool ESSFM, bool SINGLE = false, class BK = Blk<N>>
+// One block from load to output (batched launches): load, then compute.  FAST: the
+// hardware exponential, as dbp_run takes it for ESSFM plans of at most two steps.
+template <int N, bool ESSFM, bool SINGLE = false, bool FAST = false, class BK = Blk<N>>
 __device__ __forceinline__ void process_block(const FwdParams &p, BK &blk, int w, int b) {
     typename Blk<N>::Regs v;
     load_block<N, SINGLE>(p, blk, w, b, v);
@@ -174,7 +175,7 @@ __device__ __forceinline__ void process_block(const FwdParams &p, BK &blk, int w
         if (blk.t == 0) bulk_wait_read_all();
         blk.sync();
     }
-    compute_block<N, ESSFM, SINGLE, false, false, BK>(p, blk, w, b, v);
+    compute_block<N, ESSFM, SINGLE, FAST, false, BK>(p, blk, w, b, v);
 }
 
 // Persistent over blocks: CTA c processes blocks c, c + gridDim.x, ...  The twiddle
