@@ -185,6 +185,10 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     fft_e = args.fft_size or autotune(torch, "essfm", B, x, y, stream)
     fft_s = args.fft_size or autotune(torch, "ssfm", B, x, y, stream, candidates=(2048, 4096, 8192))
+    if world > 1:   # every rank runs rank 0's block lengths (set-up only, not the data path)
+        choice = torch.tensor([fft_e, fft_s], dtype=torch.int64, device="cuda")
+        dist.broadcast(choice, 0)
+        fft_e, fft_s = (int(v) for v in choice.tolist())
     pe = make_plan("essfm", B, fft_e)
     ps = make_plan("ssfm", B, fft_s)
 
