@@ -787,7 +787,8 @@ def run_case(name: str):
     """One small fixed workload per kernel, run a few times and checked, for ncu captures
     (not a benchmark): ``split`` the tcgen05 split-FP16 DFT-GEMM kernel (800 km ESSFM N_s=1
     N_c=16, N=1024, N_a=64, 64 x 2^15 samples), ``adjoint`` the reverse-mode kernel (3200 km
-    ESSFM N_s=1 N_c=16, N=4096, 64 x 2^17 samples), ``forward`` the headline kernel (3200 km
+    ESSFM N_s=1 N_c=16, N=4096, 64 x 2^17 samples; ``adjoint8192`` the same with N_s=2 at
+    N=8192), ``forward`` the headline kernel (3200 km
     ESSFM N_s=1 N_c=32, N=8192, 16 x 2^19 samples), ``batch`` the uneven-batch kernel (64
     jobs of the uneven workload, each at the shortest block length of at least twice its
     overlap)."""
@@ -829,13 +830,16 @@ def run_case(name: str):
     elif name == "adjoint":
         n, nw, kw, spans = 2 ** 17, 64, dict(method="essfm", n_steps=1, n_taps=16, coeffs=essfm_coeffs(16),
                                              fft_size=4096), N_SPANS
+    elif name == "adjoint8192":
+        n, nw, kw, spans = 2 ** 17, 64, dict(method="essfm", n_steps=2, n_taps=16, coeffs=essfm_coeffs(16),
+                                             fft_size=8192), N_SPANS
     else:
         n, nw, kw, spans = N_SAMPLES, 16, dict(method="essfm", n_steps=1, n_taps=ESSFM_TAPS,
                                                coeffs=essfm_coeffs(ESSFM_TAPS), fft_size=8192), N_SPANS
     x = torch.randn((nw, 2, n), dtype=torch.complex64, device="cuda", generator=gen) * amp
     with Plan(synth.link(spans), synth.SAMPLE_RATE, n, n_waveforms=nw, **kw) as plan:
         for _ in range(3):
-            if name == "adjoint":
+            if name.startswith("adjoint"):
                 plan.grad(x, x)
             else:
                 plan.run(x)
@@ -858,7 +862,7 @@ def main():
     ap.add_argument("--batch-jobs", type=int, default=256, help="uneven batched workload size (0: skip)")
     ap.add_argument("--no-extras", action="store_true", help="skip the precision-variant and adjoint lines")
     ap.add_argument("--sweep", action="store_true", help="3200 km method / steps / taps / block-length sweep")
-    ap.add_argument("--case", choices=["split", "adjoint", "forward", "batch"],
+    ap.add_argument("--case", choices=["split", "adjoint", "adjoint8192", "forward", "batch"],
                     help="run one small fixed workload of that kernel (for profiling) and exit")
     args = ap.parse_args()
     if args.case:
