@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         if constexpr (ESSFM) {
             __syncthreads();
             blk.stage_taps(a, p.taps_stride);
-            blk.essfm_theta(v, blk.sa, p.n_tapblk);
+            blk.template essfm_theta<-1, true>(v, blk.sa, p.n_tapblk);
         }
         const float a0 = __ldg(a);
         float4 *ck = q.ckpt + ((size_t)blkid * (ns - 1) + s) * N;
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         if constexpr (ESSFM) {
             __syncthreads();
             blk.stage_taps(a, p.taps_stride);
-            blk.essfm_theta(v, blk.sa, p.n_tapblk);
+            blk.template essfm_theta<-1, true>(v, blk.sa, p.n_tapblk);
             float *sS = blk.farr(2);
             const float *sT = blk.farr(1);
 #pragma unroll
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
                     }
                     warp_sum<8>(acc, rp + 1 + i0);
                 }
-                blk.fir16(sS, blk.farr(1), blk.sa, p.n_tapblk);
+                fir16_one_copy<N>(t, sS, blk.farr(1), blk.sa, p.n_tapblk);
             }
             __syncthreads();
             const float *sD = blk.farr(1);

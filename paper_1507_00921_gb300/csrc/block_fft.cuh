@@ -159,6 +159,9 @@ __device__ __forceinline__ float joint_intensity(float2 y0, float2 y1) {
 // GRP: the block is handled by a sub-group of N / 16 threads of a larger CTA (several
 // blocks side by side, each with its own shared-memory slice), synchronised with the
 // named barrier bar_id; otherwise by the whole CTA with __syncthreads.
+template <int N>
+__device__ __noinline__ void fir16_one_copy(int t, const float *src, float *dst, const float *a, int n_tapblk);
+
 template <int N, bool GRP = false>
 struct Blk {
     using G = Geo<N>;
@@ -501,6 +504,10 @@ struct Blk {
     // out_k = a_0 src_k + sum_{i=1}^{8 n_tapblk} a_i (src_{k-i} + src_{k+i}), read from
     // the float array src and written to dst (both pphys-indexed).  Eq. 3 when src = P.
     __device__ __forceinline__ void fir16(const float *src, float *dst, const float *a, int n_tapblk) const {
+        fir16_at(t, src, dst, a, n_tapblk);
+    }
+    static __device__ __forceinline__ void fir16_at(int t, const float *src, float *dst, const float *a,
+                                                    int n_tapblk) {
         const int k0 = 16 * t;
         float th[16];
         {
@@ -738,7 +745,9 @@ struct Blk {
 
     // The same with P in farr(0) (no halo, the wrapping fir16) and theta into farr(1): the
     // adjoint's layout, which keeps a third array (the phase gradient) in the block buffer.
-    template <int LANE = -1>
+    // ONE_COPY: the filter through fir16_one_copy (one non-inlined copy of its code for
+    // every call site of a kernel).
+    template <int LANE = -1, bool ONE_COPY = false>
     __device__ __forceinline__ void essfm_theta(const Regs &v, const float *a, int n_tapblk) {
         float *sP = farr(0);
 #pragma unroll
@@ -758,11 +767,22 @@ struct Blk {
 #ifdef DBP_FIR_TC
         fir_tc(sP, farr(1), a, n_tapblk);
 #else
-        fir16(sP, farr(1), a, n_tapblk);
+        if constexpr (ONE_COPY)
+            fir16_one_copy<N>(t, sP, farr(1), a, n_tapblk);
+        else
+            fir16(sP, farr(1), a, n_tapblk);
 #endif
         sync();
     }
 };
+
+// Blk::fir16 as a called function: kernels that filter at several places (the adjoint:
+// theta in the forward and reverse sweeps, then dL/dP) keep one copy of its code instead
+// of one inlined copy per call site.  Arguments are pointers and integers only.
+template <int N>
+__device__ __noinline__ void fir16_one_copy(int t, const float *src, float *dst, const float *a, int n_tapblk) {
+    Blk<N>::fir16_at(t, src, dst, a, n_tapblk);
+}
 
 // Multiplies the spectrum by the step's H table in shared memory (Eq. 1, inverted).
 template <int N>
