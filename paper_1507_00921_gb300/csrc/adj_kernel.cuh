@@ -337,12 +337,12 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         }
         blk.pass1_fwd(v);
         __syncthreads();
-        blk.template pass2<false>();
+        pass2_one_copy<N, false>(t, blk.xs, blk.s2);
         cp_async_wait_all();
         __syncwarp();   // passes 2 -> 3 -> 2' stay inside a warp (as in the forward kernel)
         blk.pass3(mulh);
         __syncwarp();
-        blk.template pass2<true>();
+        pass2_one_copy<N, true>(t, blk.xs, blk.s2);
         __syncthreads();
         blk.pass1_inv(v);
         const float *__restrict__ a = p.taps + p.taps_stride * s;
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         // recompute the linear sub-step, keeping U = H' X
         blk.pass1_fwd(v);
         __syncthreads();
-        blk.template pass2<false>();
+        pass2_one_copy<N, false>(t, blk.xs, blk.s2);
         cp_async_wait_all();
         __syncwarp();
         if constexpr (TM) {
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
             blk.pass3(rec);
         }
         __syncwarp();
-        blk.template pass2<true>();
+        pass2_one_copy<N, true>(t, blk.xs, blk.s2);
         __syncthreads();
         blk.pass1_inv(v);   // v = y
         const float *__restrict__ a = p.taps + p.taps_stride * s;
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         __syncthreads();
         blk.pass1_fwd(v);
         __syncthreads();
-        blk.template pass2<false>();
+        pass2_one_copy<N, false>(t, blk.xs, blk.s2);
         __syncwarp();
         float dzacc;
         if constexpr (TM) {
@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
             dzacc = adj.acc;
         }
         __syncwarp();
-        blk.template pass2<true>();
+        pass2_one_copy<N, true>(t, blk.xs, blk.s2);
         __syncthreads();
         blk.pass1_inv(v);   // v = g_x
         {

@@ -342,6 +342,11 @@ struct Blk {
     // u_k *= w_k (CONJ: conj(w_k)), k = 1 .. 15, with w from TMEM columns col ...
     template <bool CONJ>
     __device__ __forceinline__ void twiddle_tmem(float2 (&u0)[16], float2 (&u1)[16], uint32_t col = 0) const {
+        twiddle_tmem_at<CONJ>(twt, u0, u1, col);
+    }
+    template <bool CONJ>
+    static __device__ __forceinline__ void twiddle_tmem_at(uint32_t twt, float2 (&u0)[16], float2 (&u1)[16],
+                                                           uint32_t col) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             uint32_t r[8];
@@ -388,6 +393,10 @@ struct Blk {
     // TM: the twiddles come from TMEM (twiddles_to_tmem).
     template <bool INV, bool TM = false>
     __device__ __forceinline__ void pass2() {
+        pass2_at<INV, TM>(t, xs, s2, twt);
+    }
+    template <bool INV, bool TM>
+    static __device__ __forceinline__ void pass2_at(int t, float4 *xs, const float2 *s2, uint32_t twt) {
 #pragma unroll
         for (int i = 0; i < C2; ++i) {
             const int c2 = t + T * i;
@@ -405,7 +414,7 @@ struct Blk {
                 Dft<N1, false>::run(u0);
                 Dft<N1, false>::run(u1);
                 if constexpr (TM) {
-                    twiddle_tmem<false>(u0, u1, 32);
+                    twiddle_tmem_at<false>(twt, u0, u1, 32);
                 } else {
 #pragma unroll
                     for (int k = 1; k < N1; ++k) {
@@ -416,7 +425,7 @@ struct Blk {
                 }
             } else {
                 if constexpr (TM) {
-                    twiddle_tmem<true>(u0, u1, 32);
+                    twiddle_tmem_at<true>(twt, u0, u1, 32);
                 } else {
 #pragma unroll
                     for (int k = 1; k < N1; ++k) {
@@ -782,6 +791,15 @@ struct Blk {
 template <int N>
 __device__ __noinline__ void fir16_one_copy(int t, const float *src, float *dst, const float *a, int n_tapblk) {
     Blk<N>::fir16_at(t, src, dst, a, n_tapblk);
+}
+
+// Blk::pass2 with the table twiddles as a called function, for the same reason: the
+// adjoint runs pass 2 and its inverse in the forward sweep, the recomputed linear
+// sub-step and the adjoint linear sub-step.  Shared memory in and out, no register
+// arguments beyond pointers.
+template <int N, bool INV>
+__device__ __noinline__ void pass2_one_copy(int t, float4 *xs, const float2 *s2) {
+    Blk<N>::template pass2_at<INV, false>(t, xs, s2, 0u);
 }
 
 // Multiplies the spectrum by the step's H table in shared memory (Eq. 1, inverted).
