@@ -254,6 +254,73 @@ struct MidAdjointTM {
     }
 };
 
+// The adjoint's three pass-3 operations behind one run-time selector (uniform across the
+// CTA), so that one non-inlined copy of the pass-3 DFTs serves the forward sweep (x H),
+// the recomputed linear sub-step (x H, keep U) and the linear adjoint (dL/ddz, x conj(H)).
+enum { MID_MULH = 0, MID_RECOMPUTE = 1, MID_ADJOINT = 2 };
+template <int N, bool TM>
+struct MidSelect {
+    int mode;
+    const float2 *sH;
+    uint32_t ucol;   // TM: the thread's U columns
+    float4 *U;       // otherwise: the block's U scratch
+    float cphi;
+    float acc;
+    __device__ __forceinline__ void two(float2 (&u0)[16], float2 (&u1)[16], int base) {
+        if (mode == MID_MULH) {
+            MidMulH<N>{sH}.two(u0, u1, base);
+        } else if (mode == MID_RECOMPUTE) {
+            if constexpr (TM) {
+                MidRecomputeTM<N>{sH, ucol}.two(u0, u1, base);
+            } else {
+                MidRecompute<N>{sH, U}.two(u0, u1, base);
+            }
+        } else {
+            if constexpr (TM) {
+                MidAdjointTM<N> m{sH, ucol, cphi, acc};
+                m.two(u0, u1, base);
+                acc = m.acc;
+            } else {
+                MidAdjoint<N> m{sH, U, cphi, acc};
+                m.two(u0, u1, base);
+                acc = m.acc;
+            }
+        }
+    }
+    template <int R>
+    __device__ __forceinline__ void one(float2 (&u)[R], int pol, int base) {
+        if (mode == MID_MULH) {
+            MidMulH<N>{sH}.one(u, pol, base);
+        } else if (mode == MID_RECOMPUTE) {
+            if constexpr (TM) {
+                MidRecomputeTM<N>{sH, ucol}.one(u, pol, base);
+            } else {
+                MidRecompute<N>{sH, U}.one(u, pol, base);
+            }
+        } else {
+            if constexpr (TM) {
+                MidAdjointTM<N> m{sH, ucol, cphi, acc};
+                m.one(u, pol, base);
+                acc = m.acc;
+            } else {
+                MidAdjoint<N> m{sH, U, cphi, acc};
+                m.one(u, pol, base);
+                acc = m.acc;
+            }
+        }
+    }
+};
+
+// Pass 3 of the adjoint as one called copy (pointers and scalars only cross the call);
+// returns the dL/ddz accumulator of MID_ADJOINT (0 otherwise).
+template <int N, bool TM>
+__device__ __noinline__ float pass3_one_copy(int t, float4 *xs, int mode, const float2 *sH, uint32_t ucol,
+                                             float4 *U, float cphi) {
+    MidSelect<N, TM> mid{mode, sH, ucol, U, cphi, 0.f};
+    Blk<N>::pass3_at(t, xs, mid);
+    return mid.acc;
+}
+
 template <int N, bool ESSFM, bool FAST = false>
 __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel(const AdjParams q) {
     using B = Blk<N>;
@@ -328,7 +395,6 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
     }
     __syncthreads();
 
-    MidMulH<N> mulh{blk.sH};
     // ---- forward sweep: steps 0..ns-2, storing each next step's input
     for (int s = 0; s + 1 < ns; ++s) {
         if (s > 0) {
@@ -340,7 +406,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         pass2_one_copy<N, false>(t, blk.xs, blk.s2);
         cp_async_wait_all();
         __syncwarp();   // passes 2 -> 3 -> 2' stay inside a warp (as in the forward kernel)
-        blk.pass3(mulh);
+        pass3_one_copy<N, TM>(t, blk.xs, MID_MULH, blk.sH, tm_u, ub, q.cphi);
         __syncwarp();
         pass2_one_copy<N, true>(t, blk.xs, blk.s2);
         __syncthreads();
@@ -393,13 +459,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         pass2_one_copy<N, false>(t, blk.xs, blk.s2);
         cp_async_wait_all();
         __syncwarp();
-        if constexpr (TM) {
-            MidRecomputeTM<N> rec{blk.sH, tm_u};
-            blk.pass3(rec);
-        } else {
-            MidRecompute<N> rec{blk.sH, ub};
-            blk.pass3(rec);
-        }
+        pass3_one_copy<N, TM>(t, blk.xs, MID_RECOMPUTE, blk.sH, tm_u, ub, q.cphi);   // keeps U
         __syncwarp();
         pass2_one_copy<N, true>(t, blk.xs, blk.s2);
         __syncthreads();
@@ -538,16 +598,7 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
         __syncthreads();
         pass2_one_copy<N, false>(t, blk.xs, blk.s2);
         __syncwarp();
-        float dzacc;
-        if constexpr (TM) {
-            MidAdjointTM<N> adj{blk.sH, tm_u, q.cphi, 0.f};
-            blk.pass3(adj);
-            dzacc = adj.acc;
-        } else {
-            MidAdjoint<N> adj{blk.sH, ub, q.cphi, 0.f};
-            blk.pass3(adj);
-            dzacc = adj.acc;
-        }
+        const float dzacc = pass3_one_copy<N, TM>(t, blk.xs, MID_ADJOINT, blk.sH, tm_u, ub, q.cphi);
         __syncwarp();
         pass2_one_copy<N, true>(t, blk.xs, blk.s2);
         __syncthreads();

@@ -449,6 +449,10 @@ struct Blk {
     //           positions 32(t>>1).. and calls mid.one(u, pol, base).
     template <class Mid>
     __device__ __forceinline__ void pass3(Mid &mid) {
+        pass3_at(t, xs, mid);
+    }
+    template <class Mid>
+    static __device__ __forceinline__ void pass3_at(int t, float4 *xs, Mid &mid) {
         if constexpr (N0 == 16) {
             const int base = 16 * t;
             float2 u0[16], u1[16];
