@@ -329,6 +329,9 @@ __global__ void __launch_bounds__(Geo<N>::T, (N == 4096) ? 2 : 1) dbp_adj_kernel
     extern __shared__ __align__(16) unsigned char smem_raw[];
     B blk(smem_raw, threadIdx.x);
     const int t = threadIdx.x;
+    // the gather and reduction kernels that follow (launched as programmatic dependents)
+    // may be scheduled once every CTA of this grid has started; they wait for its end
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     // N = 4096 (two CTAs per SM) and N = 8192 (one): U and g in tensor memory (128 columns
     // a thread: 256 columns per CTA at N = 4096, all 512 at N = 8192), y in global scratch
     constexpr bool TM = (N == 4096 || N == 8192);

@@ -20,8 +20,33 @@
 
 namespace dbp {
 
+// Programmatic dependent launch: dbp_grad launches the kernels that follow the adjoint
+// kernel with programmatic stream serialization, so each is scheduled while its
+// predecessor drains; griddepcontrol.wait then blocks until the predecessor grid has
+// completed and its memory is visible (a no-op in a kernel launched the ordinary way).
+__device__ __forceinline__ void wait_for_predecessor() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... Params, typename... Args>
+static cudaError_t launch_dependent(void (*kernel)(Params...), dim3 grid, dim3 block, cudaStream_t st,
+                                    Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 __global__ void gather_kernel(const float4 *__restrict__ gblk, float2 *__restrict__ gin, long long n, int nb, int V,
                               int half, int N, int boundary, int n_wave) {
+    wait_for_predecessor();
+    allow_dependents();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * n_wave) return;
     const long long w = idx / n, j = idx - w * n;
@@ -72,6 +97,8 @@ __global__ void gather_kernel(const float4 *__restrict__ gblk, float2 *__restric
 // blocks in increasing block order, as gather_kernel does.
 __global__ void gather32_kernel(const float4 *__restrict__ gblk, float2 *__restrict__ gin, int n, int nb, int V,
                                 int half, int N, int boundary) {
+    wait_for_predecessor();
+    allow_dependents();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int w = blockIdx.y;
@@ -107,6 +134,8 @@ __global__ void gather32_kernel(const float4 *__restrict__ gblk, float2 *__restr
 // reproducible.
 __global__ void reduce_kernel(const float *__restrict__ part, long long rows, int stride, int segs,
                               double *__restrict__ seg_sum) {
+    wait_for_predecessor();
+    allow_dependents();
     __shared__ double sm[256];
     const int q = blockIdx.x, g = blockIdx.y;
     const long long per = (rows + segs - 1) / segs;
@@ -124,6 +153,8 @@ __global__ void reduce_kernel(const float *__restrict__ part, long long rows, in
 }
 
 __global__ void reduce_segments_kernel(const double *__restrict__ seg_sum, int stride, int segs, double *out) {
+    wait_for_predecessor();
+    allow_dependents();
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= stride) return;
     double acc = 0.0;
@@ -133,6 +164,8 @@ __global__ void reduce_segments_kernel(const double *__restrict__ seg_sum, int s
 
 __global__ void finalize_kernel(const double *sums, const float *craw, const double *geff, int ns, int nt, int nr,
                                 int per_step, float *d_coeffs, float *d_gamma, float *d_dz) {
+    wait_for_predecessor();
+    allow_dependents();
     const int t = threadIdx.x;
     const double *R = sums, *DZ = sums + (size_t)ns * nr;
     for (int q = t; q < ns * (nt + 1); q += blockDim.x) {
@@ -226,22 +259,29 @@ extern "C" int dbp_grad(dbp_plan_t *plan, const void *in, const void *grad_out, 
         const long long n = P.signal.n_samples;
         const long long span = n + (long long)P.info.n_blocks * P.info.valid + N;
         if (n >= N && span < (1LL << 30) && nw <= 65535) {
-            gather32_kernel<<<dim3((unsigned)((n + 255) / 256), (unsigned)nw), 256, 0, st>>>(
-                q.gblk, (float2 *)grad_in, (int)n, P.info.n_blocks, P.info.valid, P.info.overlap / 2, N,
-                P.signal.boundary);
+            if (launch_dependent(gather32_kernel, dim3((unsigned)((n + 255) / 256), (unsigned)nw), dim3(256), st,
+                                 (const float4 *)q.gblk, (float2 *)grad_in, (int)n, (int)P.info.n_blocks,
+                                 (int)P.info.valid, (int)(P.info.overlap / 2), N, (int)P.signal.boundary) != cudaSuccess)
+                return DBP_ERR_CUDA;
         } else {
             const long long total_s = n * nw;
-            gather_kernel<<<(unsigned)((total_s + 255) / 256), 256, 0, st>>>(
-                q.gblk, (float2 *)grad_in, n, P.info.n_blocks, P.info.valid, P.info.overlap / 2, N,
-                P.signal.boundary, nw);
+            if (launch_dependent(gather_kernel, dim3((unsigned)((total_s + 255) / 256)), dim3(256), st,
+                                 (const float4 *)q.gblk, (float2 *)grad_in, (long long)n, (int)P.info.n_blocks,
+                                 (int)P.info.valid, (int)(P.info.overlap / 2), N, (int)P.signal.boundary,
+                                 nw) != cudaSuccess)
+                return DBP_ERR_CUDA;
         }
     }
     double *sums = (double *)(sc + o_s);
     double *seg_sum = (double *)(sc + o_seg);
-    reduce_kernel<<<dim3((unsigned)stride, (unsigned)segs), 256, 0, st>>>(q.part, rows, stride, segs, seg_sum);
-    reduce_segments_kernel<<<(stride + 127) / 128, 128, 0, st>>>(seg_sum, stride, segs, sums);
-    finalize_kernel<<<1, 256, 0, st>>>(sums, P.d_craw, P.d_geff, ns, nt, nr, P.coeffs_per_step, d_coeffs, d_gamma_eff,
-                                       d_step_len);
+    if (launch_dependent(reduce_kernel, dim3((unsigned)stride, (unsigned)segs), dim3(256), st, (const float *)q.part,
+                         rows, stride, segs, seg_sum) != cudaSuccess ||
+        launch_dependent(reduce_segments_kernel, dim3((unsigned)((stride + 127) / 128)), dim3(128), st,
+                         (const double *)seg_sum, stride, segs, sums) != cudaSuccess ||
+        launch_dependent(finalize_kernel, dim3(1), dim3(256), st, (const double *)sums, (const float *)P.d_craw,
+                         (const double *)P.d_geff, ns, nt, nr, (int)P.coeffs_per_step, d_coeffs, d_gamma_eff,
+                         d_step_len) != cudaSuccess)
+        return DBP_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? DBP_OK : DBP_ERR_CUDA;
 }
 
