@@ -240,3 +240,22 @@ def test_gradient_is_bitwise_reproducible(torch_cuda):
     for a, b in zip(first, second):
         assert torch.equal(a, b)
     assert all(torch.isfinite(torch.view_as_real(t) if t.is_complex() else t).all() for t in first)
+
+
+def test_parameter_gradients_without_the_input_gradient(torch_cuda):
+    """grad_in = NULL skips the overlap-add gather, so the first reduction kernel follows the
+    adjoint kernel directly; the parameter gradients must be the same bits as with it."""
+    torch = torch_cuda
+    from paper_1507_00921_gb300 import Plan
+    n, nw = 20000, 2
+    x = torch.from_numpy(synth.random_field(nw, n, synth.dbm_to_w(2.0), seed=31).astype(np.complex64)).cuda()
+    v = torch.from_numpy(synth.random_field(nw, n, 1.0, seed=32).astype(np.complex64)).cuda()
+    for kw in (dict(method="essfm", n_steps=2, n_taps=16, fft_size=4096, coeffs=coeffs_for(16, 2, False)),
+               dict(method="ssfm", n_steps=3, fft_size=8192)):
+        with Plan(synth.link(40), FS, n, n_waveforms=nw, **kw) as plan:
+            full = plan.grad(x, v)
+            part = plan.grad(x, v, need_input=False)
+            torch.cuda.synchronize()
+        assert part[0] is None
+        for a, b in zip(full[1:], part[1:]):
+            assert torch.equal(a, b), kw
