@@ -12,7 +12,9 @@
 //      rows (segment sums, then the sum of the segments), in a fixed order;
 //   4. finalize_kernel: dL/dc_{s,i} = gamma_eff_s R_{s,i} (summed over steps when the
 //      coefficients are shared), dL/dgamma_eff_s = sum_i c_{s,i} R_{s,i}, dL/ddz_s.
-// No floating-point atomics: results are bitwise reproducible.
+// Kernels 2-4 are programmatic dependent launches (each waits for its predecessor's end
+// before reading its output).  No floating-point atomics: results are bitwise
+// reproducible.
 #include <math.h>
 #include <stdlib.h>
 
